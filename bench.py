@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the sector Hamiltonian-vector product at N_s = 15, half filling.
+
+One step = one matrix-free H*v (the hot path's core; every Lanczos and
+Green's-function step is one of these plus vector updates) on the three-orbital
+Kanamori impurity with 12 bath sites, sector (N_up, N_dn) = (7, 8),
+dim 6435^2 = 41,409,225, seeded random bath (synthetic; the paper's LDA baths
+are not available).  Inputs are larger than L2 (x is 331 MB), so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  Replicas only: with --gpus N under torchrun each
+rank runs the same workload on its own GPU, no collective on the data path
+(weak scaling); value = sum over ranks of bytes / max-over-ranks time.
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded row sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "H*v GB/s (% of HBM peak) at N_s=15"
+NS, NUP, NDN = 15, 7, 8
+SEED = 0
+
+
+def args_parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--prec", default="df64", choices=["df64", "fp64", "fp32"])
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def workload_config(prec, dim):
+    eb = 4 if prec == "fp32" else 8
+    return {"workload": f"three-orbital Kanamori impurity, N_s=15 (3 impurity + 12 bath), sector (7,8), "
+                        f"dim {dim}, matrix-free H*v",
+            "n_s": NS, "sector": [NUP, NDN], "dim": dim, "vector_format": prec,
+            "l2": f"inputs larger than L2 (x = {dim * eb / 1e6:.0f} MB, L2 ~126 MB): no flush",
+            "model": "kanamori U=2.3 J=0.4 U'=U-2J J'=J, eps_k~U[-1.5,1.5], V~U[0.1,0.4], seed 0"}
+
+
+def alg_bytes(prec, dim):
+    """Compulsory traffic of one H*v: read x once, write y once."""
+    return 2 * dim * (4 if prec == "fp32" else 8)
+
+
+# ----------------------------------------------------------- clock sampler
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def oracle_rows_rate(model, x, seconds, rng):
+    """Oracle H*v on sampled rows (literal operator application); returns
+    (rows per second, rows done, seconds)."""
+    from oracle import sector as osec
+    dim = len(x)
+    done, t0 = 0, time.perf_counter()
+    chunk = 50_000
+    while True:
+        rows = np.sort(rng.integers(0, dim, chunk))
+        osec.apply_rows(model, NUP, NDN, rows, x)
+        done += chunk
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return done / el, done, el
+
+
+def cpu_baseline(model, x, prec, seconds):
+    rng = np.random.default_rng(123)
+    rate, done, el = oracle_rows_rate(model, x, seconds, rng)
+    eb = 4 if prec == "fp32" else 8
+    return {"value": rate * 2 * eb / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} random rows of the (7,8) sector, oracle row-sampled H*v "
+                      f"(literal second-quantised operators, numpy, 1 thread), {el:.1f} s; "
+                      f"GB/s = rows/s x {2 * eb} B"}
+
+
+def traffic_for(kernel_src_sha):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("apply_src_sha") != kernel_src_sha:
+        return None
+    return d.get("bytes_per_launch")
+
+
+def src_sha():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "ed_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1004_3354_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(a):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1004_3354_gb300 as ed
+    import workloads as W
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+
+    model = W.kanamori(NS, seed=SEED)
+    dim = W.sector_dim(NS, NUP, NDN)
+    x64 = W.random_vector(dim, seed=1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(model, x64, a.prec, a.cpu_seconds)
+
+    ctx = ed.ed_ctx_create(local)
+    sec = ed.ed_sector_create(ctx, model, NUP, NDN, a.prec)
+    p = ed.PREC_NAMES[a.prec]
+    epv = ed.elems_per_value(p)
+    tdt = ed.torch_dtype(p)
+    x64d = torch.from_numpy(x64).cuda()
+    x = torch.empty(dim * epv, dtype=tdt, device="cuda")
+    ed.ed_convert(x64d, ed.ED_PREC_FP64, x, p, dim)
+    del x64d
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, a.warmup)):
+        ed.ed_apply_h(sec, x, y, stream)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(a.steps):
+        evs[i][0].record(stream)
+        ed.ed_apply_h(sec, x, y, stream)
+        evs[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [s.elapsed_time(e) for s, e in evs]
+    ms_step = total_ms / a.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    nbytes = alg_bytes(a.prec, dim)
+    value = world * nbytes / (ms_step * 1e-3) / 1e9
+
+    # end to end: pinned host x -> device, H*v, device -> pinned host y
+    h2d = d2h = dim * (4 if a.prec == "fp32" else 8)
+    hx = torch.empty(dim * epv, dtype=tdt, pin_memory=True)
+    hx.copy_(x.cpu())
+    hy = torch.empty_like(hx, pin_memory=True)
+    for _ in range(2):
+        x.copy_(hx, non_blocking=True)
+        ed.ed_apply_h(sec, x, y, stream)
+        hy.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.e2e_steps):
+        x.copy_(hx, non_blocking=True)
+        ed.ed_apply_h(sec, x, y, stream)
+        hy.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
+    e2e = {"value": world * nbytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+           "what": "pinned host x -> device, ed_apply_h, device -> pinned host y, per step"}
+
+    extras = {}
+    if not a.no_extras and rank == 0:
+        for q in ("fp64", "fp32", "df64"):
+            if q == a.prec:
+                continue
+            s2 = ed.ed_sector_create(ctx, model, NUP, NDN, q)
+            qp = ed.PREC_NAMES[q]
+            xq = torch.empty(dim * ed.elems_per_value(qp), dtype=ed.torch_dtype(qp), device="cuda")
+            ed.ed_convert(x, p, xq, qp, dim)
+            yq = torch.empty_like(xq)
+            for _ in range(3):
+                ed.ed_apply_h(s2, xq, yq, stream)
+            n_q = 10 if q != "fp64" else 5
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(n_q):
+                ed.ed_apply_h(s2, xq, yq, stream)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            msq = s0.elapsed_time(s1) / n_q
+            extras[q] = {"ms_per_apply": msq, "GB/s": alg_bytes(q, dim) / (msq * 1e-3) / 1e9}
+            del xq, yq
+            ed.ed_sector_destroy(s2)
+
+    info = ed.ed_sector_get_info(sec)
+    peak, src = peaks()
+    avg_launch = statistics.mean(launch_ms)
+    achieved = nbytes / (avg_launch * 1e-3) / 1e9
+    sha = src_sha()
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"df64": "df64 (f32 hi+lo pairs)", "fp64": "f64", "fp32": "f32 (df64 accumulate)"}[a.prec],
+        "data": "synthetic (seeded random bath)", "config": workload_config(a.prec, dim),
+        "pct_hbm_peak": round(100 * value / world / peak, 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic_for(sha),
+                     "kernel": "k_apply_rows", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
+                     "apply_src_sha": sha},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
+        "clocks": clk, "nnz_per_row": round(info.nnz_per_row, 3), "other_formats": extras,
+    }
+    ed.ed_sector_destroy(sec)
+    ed.ed_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import workloads as W
+    model = W.kanamori(NS, seed=SEED)
+    dim = W.sector_dim(NS, NUP, NDN)
+    x = W.random_vector(dim, seed=1)
+    rng = np.random.default_rng(7)
+    per_step = max(1.0, min(4.0, 120.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        oracle_rows_rate(model, x, per_step, rng)
+    rates, t0 = [], time.perf_counter()
+    rows_total = 0
+    for _ in range(a.steps):
+        r, done, el = oracle_rows_rate(model, x, per_step, rng)
+        rates.append(r)
+        rows_total += done
+    el = time.perf_counter() - t0
+    eb = 4 if a.prec == "fp32" else 8
+    value = rows_total / el * 2 * eb / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 0,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random bath)",
+           "config": workload_config(a.prec, dim),
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{rows_total} random rows over {a.steps} steps of ~{per_step:.1f} s, "
+                                      f"oracle row-sampled H*v, numpy, 1 thread"},
+           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

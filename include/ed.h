@@ -1,0 +1,220 @@
+/*
+ * ed.h -- C ABI of the GB300 exact-diagonalisation library (libedgb.so).
+ *
+ * The library applies the Hamiltonian of an impurity or cluster model to a
+ * vector inside one (N_up, N_dn) particle-number sector, runs Lanczos for the
+ * lowest eigenpairs and evaluates continued-fraction Matsubara Green's
+ * functions, all on one GPU.  The problem is the one arXiv 1004.3354 solves:
+ * diagonalise the impurity Hamiltonian for its lowest states (Sec. 2, after
+ * Eq. 3) with a Lanczos/Arnoldi solver built on repeated H*v (Sec. 3), then
+ * form G(i w_n) (Eq. 3).
+ *
+ * Conventions shared by every call
+ *  - Every call returns an ed_status.  ED_OK is 0.  On error, ed_last_error()
+ *    gives a message for the calling thread; no C++ exception crosses the ABI.
+ *  - Opaque handles (ed_ctx, ed_sector) are owned by the library and freed by
+ *    the matching *_destroy call.  Destroying NULL is ED_OK.
+ *  - Vector arguments are DEVICE pointers owned by the caller (for instance
+ *    torch.Tensor.data_ptr()).  Scalars, model parameters and returned results
+ *    are HOST memory.  `stream` is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream).  Calls are stream-ordered: they enqueue work on
+ *    `stream` and return without synchronising, except where a host result is
+ *    returned, which implies a synchronisation of `stream`.
+ *  - Basis and layout: site i is bit i of an n_s-bit spin string; each spin's
+ *    strings with the sector's particle number are listed in ascending numeric
+ *    order and a string's rank is its position there (combinatorial number
+ *    system: rank(s) = sum_k C(p_k, k+1) over the set-bit positions
+ *    p_0 < p_1 < ...).  A sector vector is the row-major D_up x D_dn array
+ *    X[r_up][r_dn], flat index r_up * D_dn + r_dn.  Fermion sign order: every
+ *    spin-up mode precedes every spin-down mode.
+ *  - Vector element formats, chosen per sector by ed_prec:
+ *      ED_PREC_FP64  IEEE double; arithmetic in native FP64.
+ *      ED_PREC_DF64  "double-float": each element is two floats {hi, lo} with
+ *                    value hi + lo (8 bytes, |lo| <= ulp(hi)); arithmetic in
+ *                    error-free float transformations (about 2^-46 relative).
+ *                    Values must lie within float's exponent range.
+ *      ED_PREC_FP32  float storage; every product and sum formed in
+ *                    double-float, the result rounded once to float.
+ */
+#ifndef ED_H
+#define ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ED_ABI_VERSION 1
+
+typedef enum ed_status {
+  ED_OK = 0,
+  ED_ERR_INVALID = 1,        /* bad argument or model */
+  ED_ERR_OOM = 2,            /* the context's HBM budget or the device is exhausted */
+  ED_ERR_CUDA = 3,           /* a CUDA runtime call failed (message has the CUDA error) */
+  ED_ERR_TIMEOUT = 4,        /* a bounded device wait ran out */
+  ED_ERR_NOT_CONVERGED = 5,  /* iteration limit reached; partial results are returned */
+  ED_ERR_BUSY = 6            /* resource in use */
+} ed_status;
+
+typedef enum ed_prec { ED_PREC_FP64 = 0, ED_PREC_DF64 = 1, ED_PREC_FP32 = 2 } ed_prec;
+
+#define ED_SPIN_UP 0
+#define ED_SPIN_DN 1
+#define ED_MAX_SITES 31
+#define ED_MAX_ORB 8
+#define ED_MAX_K 64
+
+/* Sector creation flags. */
+#define ED_SECTOR_CSR 1u   /* also build the stored CSR matrix (Fig. 1 layout), FP64 only */
+
+typedef struct ed_ctx ed_ctx;
+typedef struct ed_sector ed_sector;
+
+/*
+ * Model parameters (host memory, copied by ed_sector_create).
+ *
+ *   H = sum_{ij,s} T_ij c+_is c_js + sum_i U_site[i] n_iu n_id
+ *     + sum_{m<m'<n_orb, s,s'} (Up - J delta_ss') n_ms n_m's'
+ *     - sum_{m != m' < n_orb} [ Jsf d+_mu d_md d+_m'd d_m'u + Jph d+_mu d+_md d_m'u d_m'd ]
+ *
+ * Eq. 1 (Hubbard): T = -t, U_site = U, n_orb = 0.  Eq. 2 (Anderson impurity):
+ * star-shaped T (T_0k = V_k, T_kk = eps_k, T_00 = eps_d), U_site[0] = U,
+ * n_orb = 1.  Sec. 4 (Kanamori): T_mm = eps_m - mu, T_kk = eps_k, T_mk = V_mk,
+ * U_site[m] = U for m < n_orb, Up = U', J, Jsf = Jph = J'.
+ * Requirements: 1 <= n_s <= 31; T exactly symmetric; 0 <= n_orb <= min(n_s, 8);
+ * the sites with U_site != 0 and the n_orb orbitals are the lowest sites
+ * (any layout works, but the diagonal tables grow with the highest such site).
+ */
+typedef struct ed_model {
+  int n_s;
+  const double* T;       /* n_s * n_s, row-major */
+  const double* U_site;  /* n_s */
+  int n_orb;
+  double Up, J, Jsf, Jph;
+} ed_model;
+
+/* Sizes of a sector and its tables. */
+typedef struct ed_sector_info {
+  int n_s, n_up, n_dn, prec;
+  uint64_t D_up, D_dn, dim;
+  uint64_t hops_up, hops_dn;    /* entries in each spin's hop table */
+  uint64_t mix_up;              /* entries in the up-string spin-flip/pair-hop list */
+  uint64_t csr_nnz;             /* stored CSR entries (0 without ED_SECTOR_CSR) */
+  uint64_t table_bytes;         /* device bytes held by the sector */
+  double   nnz_per_row;         /* mean stored entries per row of H (diagonal included) */
+} ed_sector_info;
+
+/* ------------------------------------------------------------------ errors */
+/* Copy the calling thread's last error message into buf (NUL-terminated). */
+int ed_last_error(char* buf, size_t len);
+/* Compile-time ABI version of the loaded library. */
+int ed_abi_version(void);
+
+/* ----------------------------------------------------------------- context */
+/* Bind the calling thread to `device` and create a context whose own device
+ * allocations (tables, Lanczos workspaces) may not exceed hbm_budget bytes
+ * (0 = no limit beyond the device).  Errors: ED_ERR_INVALID (no such device),
+ * ED_ERR_CUDA. */
+int ed_ctx_create(int device, size_t hbm_budget, ed_ctx** out);
+int ed_ctx_destroy(ed_ctx* ctx);
+/* Bytes of device memory currently held by the context and its sectors. */
+int ed_ctx_bytes_in_use(const ed_ctx* ctx, size_t* out);
+
+/* ------------------------------------------------------------------ sector */
+/* Build the sector tables on the device (the model-dependent set-up that replaces
+ * constructing H, Table 1's T_setup): both spins' bases, hop tables with
+ * fermion signs, spin-flip/pair-hop maps and diagonal tables; with
+ * ED_SECTOR_CSR also the explicit CSR matrix (Fig. 1 layout, columns ascending,
+ * diagonal always stored).  Synchronises the context's device.
+ * Errors: ED_ERR_INVALID (model or particle numbers), ED_ERR_OOM, ED_ERR_CUDA. */
+int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn,
+                     int prec, unsigned flags, ed_sector** out);
+int ed_sector_destroy(ed_sector* s);
+int ed_sector_get_info(const ed_sector* s, ed_sector_info* out);
+/* Copy one spin's basis strings (D_spin uint32, ascending) to host memory. */
+int ed_sector_basis(const ed_sector* s, int spin, uint32_t* host_out);
+/* Copy one spin's one-body hop table to host memory: for string rank r, entries
+ * ptr[r] .. ptr[r+1]-1 give the rank tgt[k] of the string reached by moving one
+ * electron along a bond with T_ij != 0 and the matrix element val[k] =
+ * T_ij * (-1)^(occupied sites strictly between i and j), i.e. <r|H_1body|tgt>.
+ * ptr has D_spin + 1 entries, tgt/val hops_spin entries (ed_sector_info).
+ * Any output pointer may be NULL. */
+int ed_sector_hops(const ed_sector* s, int spin, uint32_t* ptr, uint32_t* tgt, double* val);
+/* Copy rows [row0, row0 + nrows) of the stored CSR (ED_SECTOR_CSR) to host
+ * memory: row_ptr (nrows + 1 entries, relative to the first copied row), cols
+ * and vals (row_ptr[nrows] entries each).  ED_ERR_INVALID without a CSR. */
+int ed_sector_csr_rows(const ed_sector* s, uint64_t row0, uint64_t nrows,
+                       uint64_t* row_ptr, uint32_t* cols, double* vals);
+
+/* ------------------------------------------------------------------- apply */
+/* y = H x inside the sector, matrix-free (elements formed on the fly, the first
+ * improvement suggested at the end of Sec. 3.2).  x and y are device arrays of
+ * `dim` elements in the sector's format; y is overwritten; x and y must not
+ * overlap.  Stream-ordered, no synchronisation, no allocation. */
+int ed_apply_h(ed_sector* s, const void* x, void* y, void* stream);
+/* y = H x from the stored CSR matrix (the Listing 1 product over Fig. 1's
+ * arrays).  Needs ED_SECTOR_CSR and ED_PREC_FP64. */
+int ed_apply_h_csr(ed_sector* s, const void* x, void* y, void* stream);
+
+/* ---------------------------------------------------------- vector helpers */
+/* Convert n elements between IEEE double and the sector-independent DF64 or
+ * FP32 formats on the device (dst and src device arrays). */
+int ed_convert(const void* src, int src_prec, void* dst, int dst_prec, uint64_t n, void* stream);
+/* Dot product <x, y> of two device vectors of n elements in format `prec`,
+ * accumulated in double; the result is written to host memory (synchronises). */
+int ed_dot(ed_ctx* ctx, const void* x, const void* y, uint64_t n, int prec, double* result, void* stream);
+
+/* ----------------------------------------------------------------- Lanczos */
+typedef struct ed_lanczos_opts {
+  int k;               /* number of lowest eigenpairs wanted (1..ED_MAX_K) */
+  double tol;          /* converged when beta_{j+1} |s_{j,i}| <= tol * max(1, |theta_i|) */
+  int max_iter;        /* Lanczos steps at most (the basis holds max_iter + 1 vectors) */
+  int check_every;     /* steps between tridiagonal solves (>= 1) */
+  uint64_t seed;       /* start vector seed when v0 == NULL */
+  const void* v0;      /* optional device start vector (sector format), NULL = seeded */
+  int reorth;          /* 1: full CGS2 reorthogonalisation against every basis vector */
+} ed_lanczos_opts;
+
+typedef struct ed_lanczos_info {
+  int iters;                    /* Lanczos steps taken */
+  int n_converged;              /* leading eigenvalues meeting tol */
+  double residual[ED_MAX_K];    /* Ritz residual estimates beta |s| */
+  double apply_ms;              /* device time in H*v (CUDA events) */
+  double total_ms;              /* wall time of the call */
+} ed_lanczos_info;
+
+/* Lowest k eigenvalues (host, ascending) and, if evecs != NULL, the Ritz vectors
+ * (device, k consecutive vectors of dim elements in the sector's format) of H in
+ * the sector, by Lanczos with full reorthogonalisation (Sec. 3: iterative
+ * solvers built on repeated H*v).  Allocates its Krylov basis from the context
+ * budget for the duration of the call.  Returns ED_ERR_NOT_CONVERGED (with the
+ * current estimates filled in) when max_iter is reached.  Synchronises. */
+int ed_lanczos(ed_sector* s, const ed_lanczos_opts* opts, double* evals,
+               void* evecs, ed_lanczos_info* info, void* stream);
+
+/* ------------------------------------------------------- Green's function */
+typedef struct ed_state {
+  int n_up, n_dn;     /* sector of the state */
+  double E;           /* its energy */
+  const void* vec;    /* device, dim elements of that sector in format `prec` */
+} ed_state;
+
+/* G(i w_n), w_n = (2n+1) pi / beta, n < n_w, of orbital `orbital` and spin
+ * `spin` (Eq. 3 with the standard sign, Im G < 0), from the given states by
+ * Lanczos continued fractions of depth `depth` in the N+1 and N-1 sectors.
+ * Z is taken over the states passed; states with e^{-beta (E - E_min)} below
+ * boltz_cut are skipped (Sec. 4 keeps about 20 states with a 1e-5 cutoff).
+ * G is host memory, 2*n_w doubles (re, im interleaved).  If coeffs != NULL it
+ * receives, per kept state and part (particle, then hole), 2 + 2*depth doubles:
+ * [n2, L, a_0..a_{depth-1}, b_0..b_{depth-1}] (b_0 = 0; L = steps taken).
+ * Builds the neighbour sectors itself.  Synchronises. */
+int ed_greens_cf(ed_ctx* ctx, const ed_model* model, int prec, int n_states,
+                 const ed_state* states, double beta, int n_w, int orbital, int spin,
+                 int depth, double boltz_cut, double* G, double* coeffs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ED_H */

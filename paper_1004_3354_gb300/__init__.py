@@ -1,0 +1,276 @@
+"""Python binding of libedgb, the GB300 exact-diagonalisation C ABI (include/ed.h).
+
+Argument marshalling only: every function below forwards to the C entry point
+of the same name; all computation runs in the library's CUDA kernels.  Device
+vectors are torch tensors on the context's device (their data_ptr() is passed),
+streams are torch.cuda.Stream objects (or None for the current stream).
+
+The library must have been built (``__graft_entry__.build()`` or
+``python paper_1004_3354_gb300/_build.py``); importing a function that needs it
+raises RuntimeError when libedgb.so is missing.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libedgb.so")
+
+ED_OK, ED_ERR_INVALID, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED, ED_ERR_BUSY = range(7)
+ED_PREC_FP64, ED_PREC_DF64, ED_PREC_FP32 = 0, 1, 2
+ED_SPIN_UP, ED_SPIN_DN = 0, 1
+ED_SECTOR_CSR = 1
+ED_MAX_K = 64
+PREC_NAMES = {"fp64": ED_PREC_FP64, "df64": ED_PREC_DF64, "fp32": ED_PREC_FP32}
+STATUS_NAMES = {0: "ED_OK", 1: "ED_ERR_INVALID", 2: "ED_ERR_OOM", 3: "ED_ERR_CUDA", 4: "ED_ERR_TIMEOUT",
+                5: "ED_ERR_NOT_CONVERGED", 6: "ED_ERR_BUSY"}
+
+
+class EdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ed_model(C.Structure):
+    _fields_ = [("n_s", C.c_int), ("T", C.POINTER(C.c_double)), ("U_site", C.POINTER(C.c_double)),
+                ("n_orb", C.c_int), ("Up", C.c_double), ("J", C.c_double), ("Jsf", C.c_double),
+                ("Jph", C.c_double)]
+
+
+class ed_sector_info(C.Structure):
+    _fields_ = [("n_s", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int), ("prec", C.c_int),
+                ("D_up", C.c_uint64), ("D_dn", C.c_uint64), ("dim", C.c_uint64),
+                ("hops_up", C.c_uint64), ("hops_dn", C.c_uint64), ("mix_up", C.c_uint64),
+                ("csr_nnz", C.c_uint64), ("table_bytes", C.c_uint64), ("nnz_per_row", C.c_double)]
+
+
+class ed_lanczos_opts(C.Structure):
+    _fields_ = [("k", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("check_every", C.c_int),
+                ("seed", C.c_uint64), ("v0", C.c_void_p), ("reorth", C.c_int)]
+
+
+class ed_lanczos_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("n_converged", C.c_int), ("residual", C.c_double * ED_MAX_K),
+                ("apply_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class ed_state(C.Structure):
+    _fields_ = [("n_up", C.c_int), ("n_dn", C.c_int), ("E", C.c_double), ("vec", C.c_void_p)]
+
+
+_lib = None
+
+_SIGS = {
+    "ed_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "ed_abi_version": (C.c_int, []),
+    "ed_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
+    "ed_ctx_destroy": (C.c_int, [C.c_void_p]),
+    "ed_ctx_bytes_in_use": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    "ed_sector_create": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.c_int, C.c_uint,
+                                   C.POINTER(C.c_void_p)]),
+    "ed_sector_destroy": (C.c_int, [C.c_void_p]),
+    "ed_sector_get_info": (C.c_int, [C.c_void_p, C.POINTER(ed_sector_info)]),
+    "ed_sector_basis": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "ed_sector_hops": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_sector_csr_rows": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_apply_h": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_apply_h_csr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_convert": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
+    "ed_dot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double),
+                         C.c_void_p]),
+    "ed_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
+                             C.POINTER(ed_lanczos_info), C.c_void_p]),
+    "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
+                               C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                               C.c_void_p, C.c_void_p]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """Load libedgb.so once (RuntimeError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(1024)
+    lib().ed_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int, allow=()):
+    if status != ED_OK and status not in allow:
+        raise EdError(status, last_error())
+    return status
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ model
+class Model:
+    """ed_model plus the host arrays it points to (kept alive here)."""
+
+    def __init__(self, m):
+        self.src = m
+        self.T = np.ascontiguousarray(m.T, dtype=np.float64)
+        self.U = np.ascontiguousarray(m.U_site, dtype=np.float64)
+        self.c = ed_model(int(m.n_s), self.T.ctypes.data_as(C.POINTER(C.c_double)),
+                          self.U.ctypes.data_as(C.POINTER(C.c_double)), int(m.n_orb), float(m.Up),
+                          float(m.J), float(m.Jsf), float(m.Jph))
+
+
+# ---------------------------------------------------------------- context
+def ed_ctx_create(device: int = 0, hbm_budget: int = 0):
+    h = C.c_void_p()
+    check(lib().ed_ctx_create(device, hbm_budget, C.byref(h)))
+    return h
+
+
+def ed_ctx_destroy(ctx):
+    return check(lib().ed_ctx_destroy(ctx))
+
+
+def ed_ctx_bytes_in_use(ctx) -> int:
+    v = C.c_size_t()
+    check(lib().ed_ctx_bytes_in_use(ctx, C.byref(v)))
+    return v.value
+
+
+def ed_sector_create(ctx, model, n_up: int, n_dn: int, prec=ED_PREC_FP64, flags: int = 0):
+    mm = model if isinstance(model, Model) else Model(model)
+    h = C.c_void_p()
+    check(lib().ed_sector_create(ctx, C.byref(mm.c), n_up, n_dn, PREC_NAMES.get(prec, prec), flags, C.byref(h)))
+    return h
+
+
+def ed_sector_destroy(sec):
+    return check(lib().ed_sector_destroy(sec))
+
+
+def ed_sector_get_info(sec) -> ed_sector_info:
+    info = ed_sector_info()
+    check(lib().ed_sector_get_info(sec, C.byref(info)))
+    return info
+
+
+def ed_sector_basis(sec, spin: int) -> np.ndarray:
+    info = ed_sector_get_info(sec)
+    n = info.D_up if spin == ED_SPIN_UP else info.D_dn
+    out = np.zeros(n, dtype=np.uint32)
+    check(lib().ed_sector_basis(sec, spin, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def ed_sector_hops(sec, spin: int):
+    info = ed_sector_get_info(sec)
+    D = info.D_up if spin == ED_SPIN_UP else info.D_dn
+    nh = info.hops_up if spin == ED_SPIN_UP else info.hops_dn
+    ptr = np.zeros(D + 1, dtype=np.uint32)
+    tgt = np.zeros(max(nh, 1), dtype=np.uint32)
+    val = np.zeros(max(nh, 1), dtype=np.float64)
+    check(lib().ed_sector_hops(sec, spin, ptr.ctypes.data_as(C.c_void_p), tgt.ctypes.data_as(C.c_void_p),
+                               val.ctypes.data_as(C.c_void_p)))
+    return ptr, tgt[:nh], val[:nh]
+
+
+def ed_sector_csr_rows(sec, row0: int, nrows: int):
+    info = ed_sector_get_info(sec)
+    rp = np.zeros(nrows + 1, dtype=np.uint64)
+    check(lib().ed_sector_csr_rows(sec, row0, nrows, rp.ctypes.data_as(C.c_void_p), None, None))
+    nnz = int(rp[-1])
+    cols = np.zeros(max(nnz, 1), dtype=np.uint32)
+    vals = np.zeros(max(nnz, 1), dtype=np.float64)
+    check(lib().ed_sector_csr_rows(sec, row0, nrows, rp.ctypes.data_as(C.c_void_p),
+                                   cols.ctypes.data_as(C.c_void_p), vals.ctypes.data_as(C.c_void_p)))
+    del info
+    return rp.astype(np.int64), cols[:nnz].astype(np.int64), vals[:nnz]
+
+
+# ------------------------------------------------------------------ apply
+def ed_apply_h(sec, x, y, stream=None):
+    return check(lib().ed_apply_h(sec, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ed_apply_h_csr(sec, x, y, stream=None):
+    return check(lib().ed_apply_h_csr(sec, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ed_convert(src, src_prec, dst, dst_prec, n: int, stream=None):
+    return check(lib().ed_convert(_ptr(src), PREC_NAMES.get(src_prec, src_prec), _ptr(dst),
+                                  PREC_NAMES.get(dst_prec, dst_prec), n, _stream(stream)))
+
+
+def ed_dot(ctx, x, y, n: int, prec, stream=None) -> float:
+    r = C.c_double()
+    check(lib().ed_dot(ctx, _ptr(x), _ptr(y), n, PREC_NAMES.get(prec, prec), C.byref(r), _stream(stream)))
+    return r.value
+
+
+# ---------------------------------------------------------------- Lanczos
+def ed_lanczos(sec, k=1, tol=1e-12, max_iter=300, check_every=10, seed=1, v0=None, reorth=True,
+               evecs=None, stream=None, allow_not_converged=False):
+    """Returns (evals ndarray[k], info, status)."""
+    o = ed_lanczos_opts(int(k), float(tol), int(max_iter), int(check_every), int(seed),
+                        None if v0 is None else v0.data_ptr(), 1 if reorth else 0)
+    ev = np.zeros(k, dtype=np.float64)
+    info = ed_lanczos_info()
+    st = lib().ed_lanczos(sec, C.byref(o), ev.ctypes.data_as(C.c_void_p), _ptr(evecs), C.byref(info),
+                          _stream(stream))
+    check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return ev, info, st
+
+
+# --------------------------------------------------------- Green's function
+def ed_greens_cf(ctx, model, prec, states, beta, n_w, orbital=0, spin=ED_SPIN_UP, depth=150,
+                 boltz_cut=1e-5, want_coeffs=False, stream=None):
+    """states: list of (n_up, n_dn, E, device tensor).  Returns G (complex ndarray[n_w])
+    and, if asked, the coefficient records (ndarray[kept*2, 2 + 2*depth])."""
+    mm = model if isinstance(model, Model) else Model(model)
+    arr = (ed_state * len(states))()
+    for i, (nu, nd, E, v) in enumerate(states):
+        arr[i] = ed_state(int(nu), int(nd), float(E), v.data_ptr())
+    G = np.zeros(2 * n_w, dtype=np.float64)
+    co = np.zeros(len(states) * 2 * (2 + 2 * depth), dtype=np.float64) if want_coeffs else None
+    check(lib().ed_greens_cf(ctx, C.byref(mm.c), PREC_NAMES.get(prec, prec), len(states), arr, float(beta),
+                             int(n_w), int(orbital), int(spin), int(depth), float(boltz_cut),
+                             G.ctypes.data_as(C.c_void_p),
+                             None if co is None else co.ctypes.data_as(C.c_void_p), _stream(stream)))
+    Gc = G[0::2] + 1j * G[1::2]
+    if want_coeffs:
+        return Gc, co.reshape(len(states) * 2, 2 + 2 * depth)
+    return Gc
+
+
+def torch_dtype(prec):
+    import torch
+    p = PREC_NAMES.get(prec, prec)
+    return {ED_PREC_FP64: torch.float64, ED_PREC_DF64: torch.float32, ED_PREC_FP32: torch.float32}[p]
+
+
+def elems_per_value(prec) -> int:
+    """torch elements per vector element (DF64 stores {hi, lo} float pairs)."""
+    return 2 if PREC_NAMES.get(prec, prec) == ED_PREC_DF64 else 1

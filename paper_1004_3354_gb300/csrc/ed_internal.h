@@ -1,0 +1,282 @@
+// Internal declarations of libedgb: device table layout, arithmetic policies,
+// allocation and error helpers.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ed.h"
+
+namespace ed {
+
+// ------------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+#define ED_TRY_CUDA(call)                                                          \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      ::ed::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e),      \
+                      __FILE__, __LINE__);                                         \
+      return ED_ERR_CUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+#define ED_TRY(call)                 \
+  do {                               \
+    int _s = (call);                 \
+    if (_s != ED_OK) return _s;      \
+  } while (0)
+
+#define ED_INVALID(...)              \
+  do {                               \
+    ::ed::set_error(__VA_ARGS__);    \
+    return ED_ERR_INVALID;           \
+  } while (0)
+
+// Launch-error check after a kernel launch (asynchronous errors surface later).
+#define ED_LAUNCH_CHECK() ED_TRY_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+  int device = 0;
+  size_t budget = 0;      // 0 = unlimited
+  size_t in_use = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  uint32_t* d_binom = nullptr;   // [33][33] binomial coefficients C(n, k)
+  double* d_red = nullptr;       // reduction scratch (partials), kRedSlots doubles
+  double* h_red = nullptr;       // pinned host mirror of d_red[0..63]
+};
+
+constexpr int kRedSlots = 8192;
+
+int dev_alloc(Ctx* c, void** p, size_t bytes);
+void dev_free(Ctx* c, void* p, size_t bytes);
+
+template <class T>
+int dev_alloc_n(Ctx* c, T** p, size_t n) {
+  return dev_alloc(c, reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// --------------------------------------------------------- sector on device
+// Per-spin tables (device pointers).  Strings are uint32 bit masks.
+struct SpinTables {
+  int n = 0;                 // particles of this spin
+  uint32_t D = 0;            // number of strings C(n_s, n)
+  uint64_t n_hops = 0;
+  uint32_t* basis = nullptr;     // [D] ascending
+  uint32_t* hop_ptr = nullptr;   // [D+1]
+  uint32_t* hop_tgt = nullptr;   // [n_hops] rank of the string reached
+  double* hop_val = nullptr;     // [n_hops] T_ij * sign
+  float2* hop_val_df = nullptr;  // [n_hops] same value split hi + lo
+  double* e = nullptr;           // [D] one-spin diagonal part
+  float2* e_df = nullptr;
+  uint32_t max_hops = 0;         // longest hop list
+};
+
+// Kernel-side view of a sector, passed by value.
+struct SectorView {
+  uint32_t D_up, D_dn;
+  int n_s, M;
+  // cross (up x down) diagonal tables over the lowest K sites, split into
+  // chunks of at most 8 sites: W_c[u_c][d_c] at w_off[c] + (u_c << w_bits[c]) + d_c
+  int n_chunks;
+  int w_bits[4];
+  uint32_t w_off[4];
+  const double* W;
+  const float2* W_df;
+  // one-body gather lists
+  const uint32_t *uh_ptr, *uh_tgt, *dh_ptr, *dh_tgt;
+  const double *uh_val, *dh_val;
+  const float2 *uh_val_df, *dh_val_df;
+  const double *e_up, *e_dn;
+  const float2 *e_up_df, *e_dn_df;
+  // spin-flip / pair-hop: per up string a list of (u_c, J * s_u, down-move table)
+  const uint32_t *mx_ptr, *mx_tgt;
+  const double* mx_val;
+  const float2* mx_val_df;
+  const uint8_t* mx_mv;
+  // down-move tables [M*M][D_dn]: (rank << 1 | sign bit) or -1
+  const int32_t* dn_move;
+};
+
+struct Sector {
+  Ctx* ctx = nullptr;
+  int n_s = 0, n_up = 0, n_dn = 0, prec = 0, M = 0, K = 0;
+  double T[ED_MAX_SITES * ED_MAX_SITES];
+  double U_site[ED_MAX_SITES];
+  double Up = 0, J = 0, Jsf = 0, Jph = 0;
+  SpinTables up, dn;
+  uint64_t dim = 0;
+  // cross tables
+  int n_chunks = 0;
+  int w_bits[4] = {0, 0, 0, 0};
+  uint32_t w_off[4] = {0, 0, 0, 0};
+  uint32_t w_size = 0;
+  double* W = nullptr;
+  float2* W_df = nullptr;
+  // mixed terms
+  uint64_t n_mix = 0;
+  uint32_t max_mix = 0;
+  uint32_t *mx_ptr = nullptr, *mx_tgt = nullptr;
+  double* mx_val = nullptr;
+  float2* mx_val_df = nullptr;
+  uint8_t* mx_mv = nullptr;
+  int32_t* dn_move = nullptr;
+  // stored CSR (optional)
+  uint64_t csr_nnz = 0;
+  uint64_t* csr_ptr = nullptr;
+  uint32_t* csr_col = nullptr;
+  double* csr_val = nullptr;
+  // bookkeeping of allocations: (pointer, bytes)
+  std::vector<std::pair<void*, size_t>> allocs;
+  size_t table_bytes = 0;
+
+  SectorView view() const;
+};
+
+template <class T>
+int sector_alloc(Sector* s, T** p, size_t n) {
+  if (n == 0) n = 1;
+  int st = dev_alloc(s->ctx, reinterpret_cast<void**>(p), n * sizeof(T));
+  if (st == ED_OK) {
+    s->allocs.push_back({(void*)*p, n * sizeof(T)});
+    s->table_bytes += n * sizeof(T);
+  }
+  return st;
+}
+
+// Builders (basis.cu, csr.cu)
+int validate_model(const ed_model* m);
+int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sector* s);
+int build_csr(Sector* s);
+void free_sector(Sector* s);
+
+// Apply entry points (apply.cu, csr.cu)
+int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st);
+int apply_h_csr(const Sector* s, const void* x, void* y, cudaStream_t st);
+
+// Vector helpers (lanczos.cu)
+size_t elem_bytes(int prec);
+int dot_async(Ctx* c, const void* x, const void* y, uint64_t n, int prec, double* d_out,
+              cudaStream_t st);
+int convert_async(const void* src, int sp, void* dst, int dp, uint64_t n, cudaStream_t st);
+
+// Sector-change maps for c+ / c (basis.cu): phi = op psi, target sector t from s.
+int apply_cop(const Sector* src, const Sector* dst, int orbital, int spin, bool dagger,
+              const void* psi, void* phi, cudaStream_t st);
+
+// Lanczos coefficient recurrence without reorthogonalisation (lanczos.cu),
+// used by the Green's function: returns n2 = <phi|phi>, a[0..L), b[0..L) (b[0]=0).
+int lanczos_coeffs(Sector* s, const void* phi, int depth, double* n2, double* a, double* b,
+                   int* L, cudaStream_t st);
+
+// ------------------------------------------------------ double-float maths
+// Error-free transformations (Knuth's TwoSum, Dekker/Kahan TwoProduct via FMA).
+// The explicit _rn intrinsics keep the compiler from contracting a product
+// into a following sum, which would break the error-free property.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// acc (hi, lo) += c (hi, lo) * x (hi, lo); the lo part accumulates lazily.
+__device__ __forceinline__ void df_mac(float2& acc, float2 c, float2 x) {
+  float p = __fmul_rn(c.x, x.x);
+  float e = __fmaf_rn(c.x, x.x, -p);
+  e = __fmaf_rn(c.x, x.y, e);
+  e = __fmaf_rn(c.y, x.x, e);
+  float s, t;
+  two_sum(acc.x, p, s, t);
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+}
+
+// acc += c * x with x a plain float.
+__device__ __forceinline__ void df_mac1(float2& acc, float2 c, float x) {
+  float p = __fmul_rn(c.x, x);
+  float e = __fmaf_rn(c.x, x, -p);
+  e = __fmaf_rn(c.y, x, e);
+  float s, t;
+  two_sum(acc.x, p, s, t);
+  acc.x = s;
+  acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ float2 df_norm(float2 a) {
+  float s, e;
+  fast_two_sum(a.x, a.y, s, e);
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  return df_norm(make_float2(s, e));
+}
+
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// double <-> double-float (set-up and boundary conversions only).
+__host__ __device__ inline float2 df_from_double(double v) {
+  float hi = (float)v;
+  float lo = (float)(v - (double)hi);
+  return make_float2(hi, lo);
+}
+__host__ __device__ inline double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// ------------------------------------------------------ arithmetic policies
+// A policy fixes the stored element type V, the accumulator A, the matrix
+// coefficient type C (read from the double or the double-float copy of a
+// table) and how one coefficient multiplies one element.
+struct PolF64 {
+  using V = double;
+  using A = double;
+  using C = double;
+  static constexpr int prec = ED_PREC_FP64;
+  __device__ static __forceinline__ A zero() { return 0.0; }
+  __device__ static __forceinline__ C ld(const double* d, const float2*, size_t k) { return d[k]; }
+  __device__ static __forceinline__ C neg(C c) { return -c; }
+  __device__ static __forceinline__ void mac(A& a, C c, V x) { a = fma(c, x, a); }
+  __device__ static __forceinline__ V out(A a) { return a; }
+};
+
+struct PolDF {
+  using V = float2;
+  using A = float2;
+  using C = float2;
+  static constexpr int prec = ED_PREC_DF64;
+  __device__ static __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ C ld(const double*, const float2* f, size_t k) { return f[k]; }
+  __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
+  __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac(a, c, x); }
+  __device__ static __forceinline__ V out(A a) { return df_norm(a); }
+};
+
+struct PolF32 {
+  using V = float;
+  using A = float2;
+  using C = float2;
+  static constexpr int prec = ED_PREC_FP32;
+  __device__ static __forceinline__ A zero() { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ C ld(const double*, const float2* f, size_t k) { return f[k]; }
+  __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
+  __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac1(a, c, x); }
+  __device__ static __forceinline__ V out(A a) { return __fadd_rn(a.x, a.y); }
+};
+
+}  // namespace ed

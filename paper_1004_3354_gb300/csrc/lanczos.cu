@@ -1,0 +1,886 @@
+// Lanczos recurrence around the sector H*v (Sec. 3: iterative eigensolvers
+// built on repeated multiplication of H by a trial vector), entirely on the
+// device:
+//   w = H v_j;  alpha_j = <v_j, w>;  w -= alpha_j v_j + beta_j v_{j-1};
+//   [full reorthogonalisation: twice  h = V^T w, w -= V h  (CGS2)]
+//   beta_{j+1} = |w|;  v_{j+1} = w / beta_{j+1}.
+// Dot products and norms are accumulated in double (FP64 vectors) or in
+// double-float (DF64 and FP32 vectors) and reduced to double; alpha, beta and
+// the tridiagonal eigenproblem are FP64.  The tridiagonal eigensolver is
+// Sturm-sequence multisection for the eigenvalues plus inverse iteration
+// (tridiagonal Gaussian elimination with partial pivoting) for the vectors.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ed_internal.h"
+
+namespace ed {
+
+size_t elem_bytes(int prec) {
+  switch (prec) {
+    case ED_PREC_FP64: return 8;
+    case ED_PREC_DF64: return 8;
+    case ED_PREC_FP32: return 4;
+  }
+  return 0;
+}
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// ------------------------------------------------ element-level helpers
+__device__ __forceinline__ void dmac(double& a, double x, double y) { a = fma(x, y, a); }
+__device__ __forceinline__ void dmac(float2& a, float2 x, float2 y) { df_mac(a, x, y); }
+__device__ __forceinline__ void dmac(float2& a, float x, float y) { df_mac1(a, make_float2(x, 0.f), y); }
+
+__device__ __forceinline__ double to_d(double a) { return a; }
+__device__ __forceinline__ double to_d(float2 a) { return (double)a.x + (double)a.y; }
+
+__device__ __forceinline__ double add_acc(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 add_acc(float2 a, float2 b) { return df_add(a, b); }
+
+__device__ __forceinline__ double shfl_x(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_x(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+template <class A>
+__device__ __forceinline__ A block_reduce(A v, A* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = add_acc(v, shfl_x(v, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  if (w == 0) {
+    v = (lane < nw) ? sh[lane] : A{};
+    for (int o = 16; o > 0; o >>= 1) v = add_acc(v, shfl_x(v, o));
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+// accumulator initialised from a stored element
+__device__ __forceinline__ double acc_of(double x) { return x; }
+__device__ __forceinline__ float2 acc_of(float2 x) { return x; }
+__device__ __forceinline__ float2 acc_of(float x) { return make_float2(x, 0.f); }
+
+__device__ __forceinline__ void amac(double& a, const double* cd, const float2*, int k, double x) {
+  a = fma(cd[k], x, a);
+}
+__device__ __forceinline__ void amac(float2& a, const double*, const float2* cf, int k, float2 x) {
+  df_mac(a, cf[k], x);
+}
+__device__ __forceinline__ void amac(float2& a, const double*, const float2* cf, int k, float x) {
+  df_mac1(a, cf[k], x);
+}
+
+__device__ __forceinline__ double store_v(double a, double*) { return a; }
+__device__ __forceinline__ float2 store_v(float2 a, float2*) { return df_norm(a); }
+__device__ __forceinline__ float store_v(float2 a, float*) { return __fadd_rn(a.x, a.y); }
+
+template <class V>
+struct AccOf;
+template <>
+struct AccOf<double> { using T = double; };
+template <>
+struct AccOf<float2> { using T = float2; };
+template <>
+struct AccOf<float> { using T = float2; };
+
+// ------------------------------------------------ reductions
+// partial[b] = sum over this block's elements of x*y (as double)
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const V* __restrict__ x, const V* __restrict__ y,
+                                                     uint64_t n, double* __restrict__ partial) {
+  using A = typename AccOf<V>::T;
+  __shared__ A sh[32];
+  A acc{};
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    dmac(acc, x[i], y[i]);
+  acc = block_reduce(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = to_d(acc);
+}
+
+// Multi-dot: partial[k * nb + b] = block b's share of <V_k, w>, k < nvec.
+template <class V, int KB>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const V* __restrict__ Vb, uint64_t stride, int k0,
+                                                          int nvec, const V* __restrict__ w, uint64_t n,
+                                                          double* __restrict__ partial) {
+  using A = typename AccOf<V>::T;
+  __shared__ A sh[32];
+  A acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = A{};
+  int kn = min(KB, nvec - k0);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    V wi = w[i];
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+      if (q < kn) dmac(acc[q], Vb[(uint64_t)(k0 + q) * stride + i], wi);
+  }
+  for (int q = 0; q < kn; ++q) {
+    A r = block_reduce(acc[q], sh);
+    if (threadIdx.x == 0) partial[(uint64_t)(k0 + q) * gridDim.x + blockIdx.x] = to_d(r);
+  }
+}
+
+// ------------------------------------------------ coefficient bookkeeping
+struct Coefs {
+  double* alpha;    // [m+1]
+  double* beta;     // [m+2], beta[0] = 0
+  double* nal_d;    // -alpha
+  float2* nal_f;
+  double* nbe_d;    // -beta
+  float2* nbe_f;
+  double* inv_d;    // 1 / beta (0 when beta vanished)
+  float2* inv_f;
+  double* h_d;      // -h (CGS projections)
+  float2* h_f;
+  double* scale;    // running max |alpha|, beta
+  int* exhausted;   // first step with a vanished beta, -1 if none
+  double* out;      // generic scalar output slots
+};
+
+enum FinishOp { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NEGH = 3, OP_NORM_INV = 4 };
+
+// Sum nb partials (one output per block of this kernel) and apply `op`.
+__global__ void __launch_bounds__(kRedThreads) k_finish(const double* __restrict__ partial, int nb, int op,
+                                                        int slot, Coefs c, double thr) {
+  __shared__ double sh[32];
+  int o = blockIdx.x;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += partial[(uint64_t)o * nb + i];
+  v = block_reduce(v, sh);
+  if (threadIdx.x != 0) return;
+  switch (op) {
+    case OP_SUM: c.out[slot + o] = v; break;
+    case OP_ALPHA:
+      c.alpha[slot] = v;
+      c.nal_d[slot] = -v;
+      c.nal_f[slot] = df_from_double(-v);
+      *c.scale = fmax(*c.scale, fabs(v));
+      break;
+    case OP_BETA: {
+      double b = sqrt(fmax(v, 0.0));
+      double sc = fmax(*c.scale, b);
+      *c.scale = sc;
+      bool dead = !(b > thr * fmax(sc, 1.0));
+      if (dead && *c.exhausted < 0) *c.exhausted = slot;
+      c.beta[slot] = dead ? 0.0 : b;
+      c.nbe_d[slot] = dead ? 0.0 : -b;
+      c.nbe_f[slot] = df_from_double(dead ? 0.0 : -b);
+      double inv = dead ? 0.0 : 1.0 / b;
+      c.inv_d[slot] = inv;
+      c.inv_f[slot] = df_from_double(inv);
+      break;
+    }
+    case OP_NEGH:
+      c.h_d[o] = -v;
+      c.h_f[o] = df_from_double(-v);
+      break;
+    case OP_NORM_INV: {
+      double b = sqrt(fmax(v, 0.0));
+      double inv = b > 0.0 ? 1.0 / b : 0.0;
+      c.out[slot] = b;
+      c.inv_d[slot] = inv;
+      c.inv_f[slot] = df_from_double(inv);
+      break;
+    }
+  }
+}
+
+// ------------------------------------------------ vector updates
+// w = w - alpha_j v - beta_j vprev  (coefficients read from device memory)
+template <class V>
+__global__ void k_lz_update(V* __restrict__ w, const V* __restrict__ v, const V* __restrict__ vp, uint64_t n,
+                            Coefs c, int j) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    auto a = acc_of(w[i]);
+    amac(a, c.nal_d, c.nal_f, j, v[i]);
+    if (vp) amac(a, c.nbe_d, c.nbe_f, j, vp[i]);
+    w[i] = store_v(a, w);
+  }
+}
+
+// w -= sum_k h_k V_k for k in [0, nvec)
+template <class V>
+__global__ void k_multi_axpy(const V* __restrict__ Vb, uint64_t stride, int nvec, V* __restrict__ w, uint64_t n,
+                             Coefs c) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    auto a = acc_of(w[i]);
+    for (int k = 0; k < nvec; ++k) amac(a, c.h_d, c.h_f, k, Vb[(uint64_t)k * stride + i]);
+    w[i] = store_v(a, w);
+  }
+}
+
+// out = w * inv[slot]
+template <class V>
+__global__ void k_scale(const V* __restrict__ w, V* __restrict__ out, uint64_t n, Coefs c, int slot) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    typename AccOf<V>::T a{};
+    amac(a, c.inv_d, c.inv_f, slot, w[i]);
+    out[i] = store_v(a, out);
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ void set_rand(double& o, float u) { o = (double)u; }
+__device__ __forceinline__ void set_rand(float2& o, float u) { o = make_float2(u, 0.f); }
+__device__ __forceinline__ void set_rand(float& o, float u) { o = u; }
+
+// Seeded start vector: uniform(-1, 1) from a counter-based hash of (seed, i).
+template <class V>
+__global__ void k_random(V* __restrict__ v, uint64_t n, uint64_t seed) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t r = mix64(seed * 0x2545f4914f6cdd1dull + i);
+    float u = (float)((r >> 40) * (1.0 / 16777216.0)) * 2.f - 1.f;
+    set_rand(v[i], u);
+  }
+}
+
+// out_i += sum_{j<m} S[i*ldS + j] V_j   for eigenvectors i in [i0, i0 + kn)
+template <class V, int KB>
+__global__ void k_ritz(const V* __restrict__ Vb, uint64_t stride, int m, const double* __restrict__ Sd,
+                       const float2* __restrict__ Sf, int ldS, int i0, int kn, V* __restrict__ out,
+                       uint64_t n, int accumulate) {
+  using A = typename AccOf<V>::T;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    A acc[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) acc[q] = (accumulate && q < kn) ? acc_of(out[(uint64_t)(i0 + q) * n + e]) : A{};
+    for (int j = 0; j < m; ++j) {
+      V vj = Vb[(uint64_t)j * stride + e];
+#pragma unroll
+      for (int q = 0; q < KB; ++q)
+        if (q < kn) amac(acc[q], Sd, Sf, (i0 + q) * ldS + j, vj);
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+      if (q < kn) out[(uint64_t)(i0 + q) * n + e] = store_v(acc[q], out);
+  }
+}
+
+__global__ void k_copy_f64(const void* __restrict__ a, void* __restrict__ b, uint64_t bytes8) {
+  const double* s = (const double*)a;
+  double* d = (double*)b;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < bytes8;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+// ------------------------------------------------ tridiagonal eigensolver
+// Sturm count: number of eigenvalues of T (alpha[0..m), beta[1..m)) below x.
+__device__ int sturm(const double* __restrict__ a, const double* __restrict__ b, int m, double x,
+                     double pivmin) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    q = (a[i] - x) - b[i] * b[i] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// Eigenvalue `blockIdx.x` (ascending) by 32-way multisection, one warp per value.
+__global__ void k_tri_eig(const double* __restrict__ a, const double* __restrict__ b, int m,
+                          double* __restrict__ theta) {
+  int i = blockIdx.x, lane = threadIdx.x;
+  double lo = a[0], hi = a[0], bmax = 0.0;
+  for (int r = 0; r < m; ++r) {
+    double off = (r > 0 ? fabs(b[r]) : 0.0) + (r + 1 < m ? fabs(b[r + 1]) : 0.0);
+    lo = fmin(lo, a[r] - off);
+    hi = fmax(hi, a[r] + off);
+    if (r > 0) bmax = fmax(bmax, fabs(b[r]));
+  }
+  double scale = fmax(fabs(lo), fabs(hi));
+  double pivmin = fmax(1e-300, 1e-290 * bmax * bmax);
+  lo -= 1e-14 * scale + 1e-300;
+  hi += 1e-14 * scale + 1e-300;
+  for (int it = 0; it < 64; ++it) {
+    if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
+    double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    int c = sturm(a, b, m, x, pivmin);
+    // first lane whose point has more than i eigenvalues below it
+    unsigned above = __ballot_sync(0xffffffffu, c > i);
+    int f = above ? __ffs(above) - 1 : 32;
+    double nlo = (f == 0) ? lo : lo + (hi - lo) * (double)f / 33.0;
+    double nhi = (f == 32) ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) theta[i] = 0.5 * (lo + hi);
+}
+
+// Inverse iteration for eigenvector blockIdx.x: solve (T - theta I) x = x_prev
+// by tridiagonal Gaussian elimination with partial pivoting (row interchanges
+// as in LAPACK's gttrf/gtts2), three sweeps.  work holds 6*ldS doubles per
+// eigenvector.  Output S[i*ldS + j], j < m, normalised, largest entry positive.
+__global__ void k_tri_vec(const double* __restrict__ a, const double* __restrict__ b, int m,
+                          const double* __restrict__ theta, double* __restrict__ S, int ldS,
+                          double* __restrict__ work) {
+  if (threadIdx.x != 0) return;
+  const int k = blockIdx.x;
+  double* x = work + (size_t)k * 6 * ldS;
+  double* dl = x + ldS;
+  double* d = dl + ldS;
+  double* du = d + ldS;
+  double* du2 = du + ldS;
+  double* piv = du2 + ldS;
+  double* s = S + (size_t)k * ldS;
+  const double th = theta[k];
+  double anorm = 0.0;
+  for (int r = 0; r < m; ++r)
+    anorm = fmax(anorm, fabs(a[r]) + (r > 0 ? fabs(b[r]) : 0.0) + (r + 1 < m ? fabs(b[r + 1]) : 0.0));
+  const double tiny = 2.2e-16 * fmax(anorm, 1e-300);
+  for (int r = 0; r < m; ++r) {
+    d[r] = a[r] - th;
+    du[r] = (r + 1 < m) ? b[r + 1] : 0.0;
+    dl[r] = (r + 1 < m) ? b[r + 1] : 0.0;  // subdiagonal (symmetric)
+    du2[r] = 0.0;
+    piv[r] = 0.0;
+  }
+  for (int r = 0; r + 1 < m; ++r) {
+    if (fabs(d[r]) >= fabs(dl[r])) {
+      double f = (d[r] != 0.0) ? dl[r] / d[r] : 0.0;
+      dl[r] = f;
+      d[r + 1] -= f * du[r];
+    } else {
+      double f = d[r] / dl[r];
+      d[r] = dl[r];
+      dl[r] = f;
+      double t = du[r];
+      du[r] = d[r + 1];
+      d[r + 1] = t - f * d[r + 1];
+      if (r + 2 < m) {
+        du2[r] = du[r + 1];
+        du[r + 1] = -f * du[r + 1];
+      }
+      piv[r] = 1.0;
+    }
+  }
+  for (int r = 0; r < m; ++r)
+    if (fabs(d[r]) < tiny) d[r] = (d[r] < 0 ? -tiny : tiny);
+  for (int r = 0; r < m; ++r) x[r] = 1.0 + 0.01 * (double)((r * 7919 + k * 104729) % 97) / 97.0;
+  for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int r = 0; r + 1 < m; ++r) {
+      if (piv[r] == 0.0) {
+        x[r + 1] -= dl[r] * x[r];
+      } else {
+        double t = x[r];
+        x[r] = x[r + 1];
+        x[r + 1] = t - dl[r] * x[r];
+      }
+    }
+    x[m - 1] /= d[m - 1];
+    if (m > 1) x[m - 2] = (x[m - 2] - du[m - 2] * x[m - 1]) / d[m - 2];
+    for (int r = m - 3; r >= 0; --r) x[r] = (x[r] - du[r] * x[r + 1] - du2[r] * x[r + 2]) / d[r];
+    double mx = 0.0;
+    for (int r = 0; r < m; ++r) mx = fmax(mx, fabs(x[r]));
+    double inv = mx > 0 ? 1.0 / mx : 0.0;
+    double nrm = 0.0;
+    for (int r = 0; r < m; ++r) {
+      x[r] *= inv;
+      nrm += x[r] * x[r];
+    }
+    inv = nrm > 0 ? 1.0 / sqrt(nrm) : 0.0;
+    for (int r = 0; r < m; ++r) x[r] *= inv;
+  }
+  int big = 0;
+  for (int r = 1; r < m; ++r)
+    if (fabs(x[r]) > fabs(x[big])) big = r;
+  double sg = x[big] < 0 ? -1.0 : 1.0;
+  for (int r = 0; r < m; ++r) s[r] = sg * x[r];
+}
+
+// Orthogonalise eigenvectors of (nearly) equal eigenvalues in order, then
+// residual estimates |beta_m s_{m-1,i}| and double-float copies.
+__global__ void k_tri_finish(const double* __restrict__ theta, int k, int m, double beta_m, double* __restrict__ S,
+                             int ldS, float2* __restrict__ Sf, double* __restrict__ resid) {
+  __shared__ double sh[32];
+  double scale = 0.0;
+  for (int i = 0; i < k; ++i) scale = fmax(scale, fabs(theta[i]));
+  for (int i = 0; i < k; ++i) {
+    double* si = S + (uint64_t)i * ldS;
+    for (int j = 0; j < i; ++j) {
+      if (fabs(theta[i] - theta[j]) > 1e-9 * fmax(scale, 1.0)) continue;
+      double* sj = S + (uint64_t)j * ldS;
+      double p = 0.0;
+      for (int r = threadIdx.x; r < m; r += blockDim.x) p += si[r] * sj[r];
+      p = block_reduce(p, sh);
+      if (threadIdx.x == 0) sh[0] = p;
+      __syncthreads();
+      p = sh[0];
+      __syncthreads();
+      for (int r = threadIdx.x; r < m; r += blockDim.x) si[r] -= p * sj[r];
+      __syncthreads();
+      double q = 0.0;
+      for (int r = threadIdx.x; r < m; r += blockDim.x) q += si[r] * si[r];
+      q = block_reduce(q, sh);
+      if (threadIdx.x == 0) sh[0] = q;
+      __syncthreads();
+      q = sh[0];
+      __syncthreads();
+      double inv = q > 0 ? 1.0 / sqrt(q) : 0.0;
+      for (int r = threadIdx.x; r < m; r += blockDim.x) si[r] *= inv;
+      __syncthreads();
+    }
+  }
+  for (int i = 0; i < k; ++i) {
+    for (int r = threadIdx.x; r < m; r += blockDim.x) Sf[(uint64_t)i * ldS + r] = df_from_double(S[(uint64_t)i * ldS + r]);
+    if (threadIdx.x == 0) resid[i] = fabs(beta_m * S[(uint64_t)i * ldS + m - 1]);
+  }
+}
+
+// ------------------------------------------------ host-side driver
+template <class V>
+struct Work {
+  Ctx* ctx;
+  cudaStream_t st;
+  uint64_t n;
+  uint32_t grid;
+  double* partial;  // ctx->d_red
+  Coefs c;
+};
+
+template <class V>
+int dot_to(Work<V>& W, const V* x, const V* y, int op, int slot, double thr = 0.0) {
+  k_dot<V><<<W.grid, kRedThreads, 0, W.st>>>(x, y, W.n, W.partial);
+  k_finish<<<1, kRedThreads, 0, W.st>>>(W.partial, (int)W.grid, op, slot, W.c, thr);
+  ED_LAUNCH_CHECK();
+  return ED_OK;
+}
+
+// CGS2 against basis vectors [0, nvec): twice h = V^T w, w -= V h.
+template <class V>
+int cgs2(Work<V>& W, const V* Vb, uint64_t stride, int nvec, V* w) {
+  if (nvec <= 0) return ED_OK;
+  int nb = (int)std::min<uint64_t>(W.grid, (uint64_t)kRedSlots / (uint64_t)nvec);
+  if (nb < 1) ED_INVALID("too many basis vectors for the reduction scratch (%d)", nvec);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int k0 = 0; k0 < nvec; k0 += 8)
+      k_multidot<V, 8><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
+    k_finish<<<nvec, kRedThreads, 0, W.st>>>(W.partial, nb, OP_NEGH, 0, W.c, 0.0);
+    k_multi_axpy<V><<<W.grid, 256, 0, W.st>>>(Vb, stride, nvec, w, W.n, W.c);
+    ED_LAUNCH_CHECK();
+  }
+  return ED_OK;
+}
+
+struct DevBuf {
+  Ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  int alloc(Ctx* c, size_t b) {
+    ctx = c;
+    bytes = b ? b : 1;
+    return dev_alloc(c, &p, bytes);
+  }
+  ~DevBuf() {
+    if (p) dev_free(ctx, p, bytes);
+  }
+};
+
+// Carves typed arrays out of one allocation (256-byte aligned).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+size_t coef_bytes(int mmax, int k) {
+  size_t m2 = (size_t)mmax + 2;
+  return 256 * 64 + m2 * 8 * 16 + (size_t)k * m2 * 8 * 8 + 2048;
+}
+
+Coefs carve_coefs(Carve& cv, int mmax) {
+  Coefs c;
+  size_t m2 = (size_t)mmax + 2;
+  c.alpha = cv.take<double>(m2);
+  c.beta = cv.take<double>(m2);
+  c.nal_d = cv.take<double>(m2);
+  c.nal_f = cv.take<float2>(m2);
+  c.nbe_d = cv.take<double>(m2);
+  c.nbe_f = cv.take<float2>(m2);
+  c.inv_d = cv.take<double>(m2);
+  c.inv_f = cv.take<float2>(m2);
+  c.h_d = cv.take<double>(m2);
+  c.h_f = cv.take<float2>(m2);
+  c.scale = cv.take<double>(1);
+  c.exhausted = cv.take<int>(1);
+  c.out = cv.take<double>(64);
+  return c;
+}
+
+__global__ void k_init_coefs(Coefs c, int m2) {
+  for (int i = threadIdx.x; i < m2; i += blockDim.x) {
+    c.alpha[i] = 0;
+    c.beta[i] = 0;
+    c.nal_d[i] = 0;
+    c.nal_f[i] = make_float2(0, 0);
+    c.nbe_d[i] = 0;
+    c.nbe_f[i] = make_float2(0, 0);
+    c.inv_d[i] = 0;
+    c.inv_f[i] = make_float2(0, 0);
+    c.h_d[i] = 0;
+    c.h_f[i] = make_float2(0, 0);
+  }
+  if (threadIdx.x == 0) {
+    *c.scale = 0.0;
+    *c.exhausted = -1;
+  }
+}
+
+// Solve the m x m tridiagonal problem for its k lowest pairs.
+int tridiag(Ctx* ctx, cudaStream_t st, const Coefs& c, int m, int k, double beta_m, double* theta,
+            double* S, float2* Sf, int ldS, double* resid, double* work) {
+  k_tri_eig<<<k, 32, 0, st>>>(c.alpha, c.beta, m, theta);
+  k_tri_vec<<<k, 32, 0, st>>>(c.alpha, c.beta, m, theta, S, ldS, work);
+  k_tri_finish<<<1, 128, 0, st>>>(theta, k, m, beta_m, S, ldS, Sf, resid);
+  ED_LAUNCH_CHECK();
+  (void)ctx;
+  return ED_OK;
+}
+
+template <class V>
+int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
+                 cudaStream_t st) {
+  auto t_start = std::chrono::steady_clock::now();
+  Ctx* ctx = s->ctx;
+  const uint64_t n = s->dim;
+  const int k = o->k;
+  const int reorth = o->reorth ? 1 : 0;
+  int mmax = (int)std::min<uint64_t>((uint64_t)o->max_iter, n);
+  if (mmax < 1) mmax = 1;
+  const int check_every = std::max(1, o->check_every);
+  const int kk = std::min<int>(k, (int)n);
+
+  // workspace: basis (mmax + 1 vectors with reorthogonalisation, else 3), w
+  size_t eb = sizeof(V);
+  int nvec_store = reorth ? (mmax + 1) : 3;
+  DevBuf vb, cb, v0b;
+  ED_TRY(vb.alloc(ctx, ((size_t)nvec_store + 1) * n * eb));
+  ED_TRY(cb.alloc(ctx, coef_bytes(mmax, std::max(kk, 1))));
+  V* Vbase = static_cast<V*>(vb.p);
+  V* w = Vbase + (size_t)nvec_store * n;
+  if (!reorth) ED_TRY(v0b.alloc(ctx, n * eb));
+  Carve cv{static_cast<char*>(cb.p)};
+  Coefs c = carve_coefs(cv, mmax);
+  int ldS = mmax + 1;
+  double* theta = cv.take<double>(ED_MAX_K);
+  double* resid = cv.take<double>(ED_MAX_K);
+  double* Sd = cv.take<double>((size_t)ldS * std::max(kk, 1));
+  float2* Sf = cv.take<float2>((size_t)ldS * std::max(kk, 1));
+  double* twork = cv.take<double>((size_t)6 * ldS * std::max(kk, 1));
+
+  Work<V> W;
+  W.ctx = ctx;
+  W.st = st;
+  W.n = n;
+  W.grid = (uint32_t)std::min<uint64_t>((n + kRedThreads - 1) / kRedThreads, (uint64_t)ctx->num_sms * 8);
+  if (W.grid == 0) W.grid = 1;
+  W.partial = ctx->d_red;
+  W.c = c;
+  uint32_t vgrid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 16);
+  if (vgrid == 0) vgrid = 1;
+
+  k_init_coefs<<<1, 256, 0, st>>>(c, mmax + 2);
+  auto vec = [&](int j) -> V* { return reorth ? Vbase + (size_t)j * n : Vbase + (size_t)(j % 3) * n; };
+
+  // start vector
+  if (o->v0) {
+    ED_TRY_CUDA(cudaMemcpyAsync(w, o->v0, n * eb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    k_random<V><<<vgrid, 256, 0, st>>>(w, n, o->seed);
+  }
+  ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_NORM_INV, 0));
+  k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(0), n, c, 0);
+  ED_LAUNCH_CHECK();
+  if (!reorth) ED_TRY_CUDA(cudaMemcpyAsync(v0b.p, vec(0), n * eb, cudaMemcpyDeviceToDevice, st));
+
+  // one event pair per step to time the H*v launches
+  std::vector<cudaEvent_t> evs(2 * (size_t)mmax);
+  for (auto& e : evs) ED_TRY_CUDA(cudaEventCreate(&e));
+  struct EvGuard {
+    std::vector<cudaEvent_t>* v;
+    ~EvGuard() {
+      for (auto e : *v) cudaEventDestroy(e);
+    }
+  } evguard{&evs};
+  double apply_ms = 0.0;
+  int n_timed = 0;
+
+  std::vector<double> h_theta(ED_MAX_K), h_res(ED_MAX_K);
+  int m = 0;          // current Krylov dimension
+  int n_conv = 0;
+  double beta_last = 0.0;
+  bool done = false;
+  int status = ED_OK;
+  int restarts = 0;
+  const double thr = 1e-13;
+  int j = 0;
+  while (!done) {
+    for (; j < mmax; ++j) {
+      V* vj = vec(j);
+      V* vjm = (j > 0) ? vec(j - 1) : nullptr;
+      ED_TRY_CUDA(cudaEventRecord(evs[2 * j], st));
+      ED_TRY(apply_h(s, vj, w, st));
+      ED_TRY_CUDA(cudaEventRecord(evs[2 * j + 1], st));
+      n_timed = std::max(n_timed, j + 1);
+      ED_TRY(dot_to(W, (const V*)vj, (const V*)w, OP_ALPHA, j));
+      k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vj, vjm, n, c, j);
+      ED_LAUNCH_CHECK();
+      if (reorth) ED_TRY(cgs2(W, (const V*)Vbase, n, j + 1, w));
+      ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_BETA, j + 1, thr));
+      k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(j + 1), n, c, j + 1);
+      ED_LAUNCH_CHECK();
+      m = j + 1;
+      bool check = ((m % check_every) == 0) || (m == mmax) || (n <= 4096);
+      if (!check) continue;
+      // exhausted Krylov space?
+      int ex = -1;
+      ED_TRY_CUDA(cudaMemcpyAsync(ctx->h_red, c.exhausted, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ED_TRY_CUDA(cudaStreamSynchronize(st));
+      std::memcpy(&ex, ctx->h_red, sizeof(int));
+      if (ex >= 0) {
+        m = ex;  // T is complete up to here; later steps are discarded
+        ++j;
+        break;
+      }
+      int kc = std::min(kk, m);
+      ED_TRY(tridiag(ctx, st, c, m, kc, 0.0, theta, Sd, Sf, ldS, resid, twork));
+      // residuals use beta_{m}
+      ED_TRY_CUDA(cudaMemcpyAsync(ctx->h_red, c.beta + m, sizeof(double), cudaMemcpyDeviceToHost, st));
+      ED_TRY_CUDA(cudaMemcpyAsync(ctx->h_red + 1, theta, kc * sizeof(double), cudaMemcpyDeviceToHost, st));
+      ED_TRY_CUDA(cudaStreamSynchronize(st));
+      beta_last = ctx->h_red[0];
+      std::memcpy(h_theta.data(), ctx->h_red + 1, kc * sizeof(double));
+      // residual = beta_m * |last component|
+      std::vector<double> last(kc);
+      for (int i = 0; i < kc; ++i)
+        ED_TRY_CUDA(cudaMemcpyAsync(&last[i], Sd + (size_t)i * ldS + m - 1, sizeof(double),
+                                    cudaMemcpyDeviceToHost, st));
+      ED_TRY_CUDA(cudaStreamSynchronize(st));
+      n_conv = 0;
+      for (int i = 0; i < kc; ++i) {
+        h_res[i] = std::fabs(beta_last * last[i]);
+        if (h_res[i] <= o->tol * std::max(1.0, std::fabs(h_theta[i])) && n_conv == i) ++n_conv;
+      }
+      if (kc >= kk && n_conv >= kk) {
+        ++j;
+        done = true;
+        break;
+      }
+    }
+    if (done) break;
+    if (j >= mmax && m >= mmax) {
+      status = ED_ERR_NOT_CONVERGED;
+      break;
+    }
+    // Krylov space exhausted at m: finished if it spans the sector or we have
+    // k values already; otherwise restart from a fresh orthogonal vector.
+    {
+      int kc = std::min(kk, m);
+      ED_TRY(tridiag(ctx, st, c, m, kc, 0.0, theta, Sd, Sf, ldS, resid, twork));
+      ED_TRY_CUDA(cudaMemcpyAsync(ctx->h_red, theta, kc * sizeof(double), cudaMemcpyDeviceToHost, st));
+      ED_TRY_CUDA(cudaStreamSynchronize(st));
+      std::memcpy(h_theta.data(), ctx->h_red, kc * sizeof(double));
+      for (int i = 0; i < kc; ++i) h_res[i] = 0.0;
+      n_conv = kc;
+      beta_last = 0.0;
+      if (!reorth || (uint64_t)m >= n || m >= mmax || kc >= kk) {
+        done = true;
+        break;
+      }
+      // new random direction, orthogonalised against V[0..m)
+      ++restarts;
+      k_random<V><<<vgrid, 256, 0, st>>>(w, n, o->seed + 7919ull * restarts);
+      ED_TRY(cgs2(W, (const V*)Vbase, n, m, w));
+      ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_NORM_INV, 1));
+      k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(m), n, c, 1);
+      // beta[m] = 0 splits T; reset the exhaustion flag
+      double zero = 0.0;
+      int neg = -1;
+      ED_TRY_CUDA(cudaMemcpyAsync(c.beta + m, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+      ED_TRY_CUDA(cudaMemcpyAsync(c.nbe_d + m, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+      float2 zf = make_float2(0.f, 0.f);
+      ED_TRY_CUDA(cudaMemcpyAsync(c.nbe_f + m, &zf, sizeof(float2), cudaMemcpyHostToDevice, st));
+      ED_TRY_CUDA(cudaMemcpyAsync(c.exhausted, &neg, sizeof(int), cudaMemcpyHostToDevice, st));
+      ED_TRY_CUDA(cudaStreamSynchronize(st));
+      j = m;
+    }
+  }
+
+  int kc = std::min(kk, m);
+  for (int i = 0; i < kc; ++i) evals[i] = h_theta[i];
+  for (int i = kc; i < k; ++i) evals[i] = NAN;
+  if (info) {
+    info->iters = m;
+    info->n_converged = std::min(n_conv, kc);
+    for (int i = 0; i < ED_MAX_K; ++i) info->residual[i] = (i < kc) ? h_res[i] : 0.0;
+  }
+  if (evecs && kc > 0) {
+    // S for the final m
+    ED_TRY(tridiag(ctx, st, c, m, kc, 0.0, theta, Sd, Sf, ldS, resid, twork));
+    V* out = static_cast<V*>(evecs);
+    if (reorth) {
+      for (int i0 = 0; i0 < kc; i0 += 8)
+        k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vbase, n, m, Sd, Sf, ldS, i0, std::min(8, kc - i0), out, n, 0);
+      ED_LAUNCH_CHECK();
+    } else {
+      // second pass: regenerate v_j with the stored alpha, beta and accumulate
+      ED_TRY_CUDA(cudaMemsetAsync(out, 0, (size_t)kc * n * eb, st));
+      ED_TRY_CUDA(cudaMemcpyAsync(vec(0), v0b.p, n * eb, cudaMemcpyDeviceToDevice, st));
+      for (int jj = 0; jj < m; ++jj) {
+        for (int i0 = 0; i0 < kc; i0 += 8)
+          k_ritz<V, 8><<<vgrid, 256, 0, st>>>(vec(jj), n, 1, Sd + jj, Sf + jj, ldS, i0, std::min(8, kc - i0), out,
+                                              n, 1);
+        if (jj + 1 == m) break;
+        ED_TRY(apply_h(s, vec(jj), w, st));
+        k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vec(jj), jj > 0 ? vec(jj - 1) : nullptr, n, c, jj);
+        k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(jj + 1), n, c, jj + 1);
+        ED_LAUNCH_CHECK();
+      }
+    }
+  }
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int q = 0; q < n_timed; ++q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, evs[2 * q], evs[2 * q + 1]) == cudaSuccess) apply_ms += ms;
+  }
+  if (info) info->apply_ms = apply_ms;
+  if (info)
+    info->total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (status != ED_OK) set_error("Lanczos did not converge in %d steps", mmax);
+  return status;
+}
+
+template <class V>
+int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, double* b, int* L,
+                cudaStream_t st) {
+  Ctx* ctx = s->ctx;
+  const uint64_t n = s->dim;
+  size_t eb = sizeof(V);
+  DevBuf vb, cb;
+  ED_TRY(vb.alloc(ctx, 4 * n * eb));
+  ED_TRY(cb.alloc(ctx, coef_bytes(depth, 1)));
+  V* vecs = static_cast<V*>(vb.p);
+  V* w = vecs + 3 * n;
+  Carve cv{static_cast<char*>(cb.p)};
+  Coefs c = carve_coefs(cv, depth);
+  Work<V> W;
+  W.ctx = ctx;
+  W.st = st;
+  W.n = n;
+  W.grid = (uint32_t)std::min<uint64_t>((n + kRedThreads - 1) / kRedThreads, (uint64_t)ctx->num_sms * 8);
+  if (W.grid == 0) W.grid = 1;
+  W.partial = ctx->d_red;
+  W.c = c;
+  uint32_t vgrid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 16);
+  if (vgrid == 0) vgrid = 1;
+  k_init_coefs<<<1, 256, 0, st>>>(c, depth + 2);
+  const V* ph = static_cast<const V*>(phi);
+  ED_TRY(dot_to(W, ph, ph, OP_NORM_INV, 0));
+  k_scale<V><<<vgrid, 256, 0, st>>>(ph, vecs, n, c, 0);
+  ED_LAUNCH_CHECK();
+  const double thr = 1e-12;
+  for (int j = 0; j < depth; ++j) {
+    V* vj = vecs + (size_t)(j % 3) * n;
+    V* vjm = j > 0 ? vecs + (size_t)((j + 2) % 3) * n : nullptr;
+    ED_TRY(apply_h(s, vj, w, st));
+    ED_TRY(dot_to(W, (const V*)vj, (const V*)w, OP_ALPHA, j));
+    if (j + 1 == depth) break;
+    k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vj, vjm, n, c, j);
+    ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_BETA, j + 1, thr));
+    k_scale<V><<<vgrid, 256, 0, st>>>(w, vecs + (size_t)((j + 1) % 3) * n, n, c, j + 1);
+    ED_LAUNCH_CHECK();
+  }
+  std::vector<double> hb(depth + 1), ha(depth);
+  double norm = 0.0;
+  int ex = -1;
+  ED_TRY_CUDA(cudaMemcpyAsync(ha.data(), c.alpha, depth * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ED_TRY_CUDA(cudaMemcpyAsync(hb.data(), c.beta, (depth + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  ED_TRY_CUDA(cudaMemcpyAsync(&norm, c.out, sizeof(double), cudaMemcpyDeviceToHost, st));
+  ED_TRY_CUDA(cudaMemcpyAsync(&ex, c.exhausted, sizeof(int), cudaMemcpyDeviceToHost, st));
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
+  *n2 = norm * norm;
+  int len = (ex >= 0) ? ex : depth;
+  if (norm == 0.0) len = 0;
+  *L = len;
+  for (int i = 0; i < depth; ++i) {
+    a[i] = (i < len) ? ha[i] : 0.0;
+    b[i] = (i < len && i > 0) ? hb[i] : 0.0;
+  }
+  return ED_OK;
+}
+
+}  // namespace
+
+int dot_async(Ctx* c, const void* x, const void* y, uint64_t n, int prec, double* d_out, cudaStream_t st) {
+  uint32_t grid = (uint32_t)std::min<uint64_t>((n + kRedThreads - 1) / kRedThreads, (uint64_t)c->num_sms * 8);
+  if (grid == 0) grid = 1;
+  Coefs cf{};
+  cf.out = d_out;
+  switch (prec) {
+    case ED_PREC_FP64:
+      k_dot<double><<<grid, kRedThreads, 0, st>>>((const double*)x, (const double*)y, n, c->d_red);
+      break;
+    case ED_PREC_DF64:
+      k_dot<float2><<<grid, kRedThreads, 0, st>>>((const float2*)x, (const float2*)y, n, c->d_red);
+      break;
+    case ED_PREC_FP32:
+      k_dot<float><<<grid, kRedThreads, 0, st>>>((const float*)x, (const float*)y, n, c->d_red);
+      break;
+    default: ED_INVALID("unknown precision %d", prec);
+  }
+  k_finish<<<1, kRedThreads, 0, st>>>(c->d_red, (int)grid, OP_SUM, 0, cf, 0.0);
+  ED_LAUNCH_CHECK();
+  return ED_OK;
+}
+
+int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
+                cudaStream_t st) {
+  switch (s->prec) {
+    case ED_PREC_FP64: return lanczos_impl<double>(s, o, evals, evecs, info, st);
+    case ED_PREC_DF64: return lanczos_impl<float2>(s, o, evals, evecs, info, st);
+    case ED_PREC_FP32: return lanczos_impl<float>(s, o, evals, evecs, info, st);
+  }
+  ED_INVALID("unknown precision");
+}
+
+int lanczos_coeffs(Sector* s, const void* phi, int depth, double* n2, double* a, double* b, int* L,
+                   cudaStream_t st) {
+  switch (s->prec) {
+    case ED_PREC_FP64: return coeffs_impl<double>(s, phi, depth, n2, a, b, L, st);
+    case ED_PREC_DF64: return coeffs_impl<float2>(s, phi, depth, n2, a, b, L, st);
+    case ED_PREC_FP32: return coeffs_impl<float>(s, phi, depth, n2, a, b, L, st);
+  }
+  ED_INVALID("unknown precision");
+}
+
+}  // namespace ed

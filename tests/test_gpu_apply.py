@@ -1,0 +1,173 @@
+"""Matrix-free H*v through the C ABI vs the oracle's explicit sector H.
+
+FP64 and DF64: ||y - y_ref|| / ||y_ref|| <= 1e-12 (the FP64 target).
+FP32 vectors: compared with the oracle applied to the float-rounded input;
+the only error left is the single rounding of each output to float, so the
+bound is 2^-24 ~ 6e-8 per element; the test allows 1e-6 norm-wise.
+Small sectors are checked element by element on every row; large ones (row
+lengths that select the row-staged kernel, and the full N_s=15 half-filled
+sector the benchmark times) on sampled rows, first/last/ragged rows included.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sector as osec
+from tests._gpu import ensure_built, torch_cuda, to_dev, to_host, empty_vec, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "df64": 1e-12, "fp32": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    ed = ensure_built()
+    ctx = ed.ed_ctx_create(0)
+    yield ed, ctx, torch
+    ed.ed_ctx_destroy(ctx)
+
+
+_CSR = {}
+
+
+def oracle_csr(name, m, nu, nd):
+    if name not in _CSR:
+        _CSR[name] = osec.build_csr(m, nu, nd)
+    return _CSR[name]
+
+
+def run_apply(ed, ctx, torch, m, nu, nd, prec, x):
+    sec = ed.ed_sector_create(ctx, m, nu, nd, prec)
+    try:
+        n = len(x)
+        xd = to_dev(x, prec, ed, torch)
+        yd = empty_vec(n, prec, ed, torch)
+        ed.ed_apply_h(sec, xd, yd)
+        torch.cuda.synchronize()
+        return to_host(yd, prec, n, ed, torch)
+    finally:
+        ed.ed_sector_destroy(sec)
+
+
+def input_for(prec, x):
+    return x.astype(np.float32).astype(np.float64) if prec == "fp32" else x
+
+
+FULL = [
+    ("C0 AIM N_s=6 (3,3)", lambda: W.aim(6, seed=0), 3, 3),
+    ("Kanamori N_s=8 (4,3)", lambda: W.kanamori(8, seed=1), 4, 3),
+    ("Kanamori M=2 N_s=7 (3,4)", lambda: W.kanamori(7, seed=5, n_orb=2), 3, 4),
+    ("Hubbard ring N_s=10 (5,4) two diagonal chunks", lambda: W.hubbard_cluster(10, tp=0.3), 5, 4),
+    ("Hubbard ring N_s=12 (6,6) K=12", lambda: W.hubbard_cluster(12, tp=0.2), 6, 6),
+    ("atom (2,1)", lambda: W.atom(3), 2, 1),
+    ("dim 1 (0,0)", lambda: W.kanamori(8, seed=2), 0, 0),
+    ("dim 1 full (8,8)", lambda: W.kanamori(8, seed=2), 8, 8),
+    ("D_up 1 (0,3)", lambda: W.kanamori(8, seed=2), 0, 3),
+    ("D_dn 1 (5,8)", lambda: W.kanamori(8, seed=2), 5, 8),
+    ("Kanamori 4 orbitals N_s=9 (4,5)", lambda: W.kanamori(9, seed=4, n_orb=4), 4, 5),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("name,mk,nu,nd", FULL, ids=[c[0] for c in FULL])
+def test_apply_full_sector(env, name, mk, nu, nd, prec):
+    ed, ctx, torch = env
+    m = mk()
+    H = oracle_csr(name, m, nu, nd)
+    x = W.random_vector(H.shape[0], seed=1)
+    xin = input_for(prec, x)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x)
+    ref = H @ xin
+    assert rel_err(y, ref) <= TOL[prec], rel_err(y, ref)
+    if prec == "fp64":
+        assert np.max(np.abs(y - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def sample_rows(dim, D_dn, k=2500, seed=3):
+    rng = np.random.default_rng(seed)
+    rows = set(rng.integers(0, dim, k).tolist())
+    rows |= {0, 1, D_dn - 1, D_dn, dim - 1, dim - 2, dim // 2, (dim // D_dn - 1) * D_dn}
+    return np.array(sorted(r for r in rows if 0 <= r < dim))
+
+
+SAMPLED = [
+    ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6),
+    ("Kanamori N_s=13 (6,7) row-staged", lambda: W.kanamori(13, seed=3), 6, 7),
+    ("Hubbard ring N_s=13 (7,6) row-staged K=13", lambda: W.hubbard_cluster(13, tp=0.1), 7, 6),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("name,mk,nu,nd", SAMPLED, ids=[c[0] for c in SAMPLED])
+def test_apply_sampled_rows(env, name, mk, nu, nd, prec):
+    ed, ctx, torch = env
+    m = mk()
+    D_dn = len(osec.spin_basis(m.n_s, nd))
+    dim = len(osec.spin_basis(m.n_s, nu)) * D_dn
+    x = W.random_vector(dim, seed=2)
+    xin = input_for(prec, x)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x)
+    rows = sample_rows(dim, D_dn)
+    ref = osec.apply_rows(m, nu, nd, rows, xin)
+    assert rel_err(y[rows], ref) <= TOL[prec], rel_err(y[rows], ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_apply_n15_half_filling_sampled(env, prec):
+    """The N_s=15 (7,8) sector (dim 41,409,225) in the launch configuration the
+    benchmark times, checked on sampled rows."""
+    ed, ctx, torch = env
+    m = W.kanamori(15, seed=0)
+    nu, nd = 7, 8
+    dim = 6435 * 6435
+    x = W.random_vector(dim, seed=1)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x)
+    rows = sample_rows(dim, 6435, k=1500)
+    ref = osec.apply_rows(m, nu, nd, rows, x)
+    assert rel_err(y[rows], ref) <= 1e-12
+
+
+def test_apply_csr_variant(env):
+    ed, ctx, torch = env
+    for m, nu, nd in ((W.aim(6), 3, 3), (W.kanamori(10, seed=6), 5, 5)):
+        H = osec.build_csr(m, nu, nd)
+        sec = ed.ed_sector_create(ctx, m, nu, nd, "fp64", ed.ED_SECTOR_CSR)
+        try:
+            x = W.random_vector(H.shape[0], seed=4)
+            xd = torch.from_numpy(x).cuda()
+            y1 = torch.empty_like(xd)
+            y2 = torch.empty_like(xd)
+            ed.ed_apply_h_csr(sec, xd, y1)
+            ed.ed_apply_h(sec, xd, y2)
+            torch.cuda.synchronize()
+            ref = H @ x
+            assert rel_err(y1.cpu().numpy(), ref) <= 1e-12
+            assert rel_err(y2.cpu().numpy(), y1.cpu().numpy()) <= 1e-13
+        finally:
+            ed.ed_sector_destroy(sec)
+
+
+def test_apply_is_deterministic_and_symmetric(env):
+    ed, ctx, torch = env
+    m = W.kanamori(12, seed=0)
+    sec = ed.ed_sector_create(ctx, m, 6, 6, "fp64")
+    try:
+        n = 924 * 924
+        a = torch.from_numpy(W.random_vector(n, 5)).cuda()
+        b = torch.from_numpy(W.random_vector(n, 6)).cuda()
+        ha, hb, ha2 = torch.empty_like(a), torch.empty_like(a), torch.empty_like(a)
+        ed.ed_apply_h(sec, a, ha)
+        ed.ed_apply_h(sec, b, hb)
+        ed.ed_apply_h(sec, a, ha2)
+        torch.cuda.synchronize()
+        assert torch.equal(ha, ha2)
+        # <b, H a> = <H b, a>
+        lhs = float(torch.dot(b, ha))
+        rhs = float(torch.dot(hb, a))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+        with pytest.raises(ed.EdError):
+            ed.ed_apply_h(sec, a, a)
+    finally:
+        ed.ed_sector_destroy(sec)
