@@ -40,7 +40,7 @@ SEED = 0
 def args_parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=400)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="df64", choices=["df64", "fp64", "fp32"])
@@ -81,7 +81,7 @@ class Clocks:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -155,7 +155,7 @@ def traffic_for(kernel_src_sha):
 
 def src_sha():
     h = hashlib.sha256()
-    for f in ("apply.cu", "ed_internal.h"):
+    for f in ("apply_fast.cu", "ed_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1004_3354_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -299,7 +299,7 @@ def run_ours(a):
         "pct_hbm_peak": round(100 * value / world / peak, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic_for(sha),
-                     "kernel": "k_apply_rows", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "k_apply_fast", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
                      "apply_src_sha": sha},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,

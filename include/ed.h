@@ -67,7 +67,8 @@ typedef enum ed_prec { ED_PREC_FP64 = 0, ED_PREC_DF64 = 1, ED_PREC_FP32 = 2 } ed
 #define ED_MAX_K 64
 
 /* Sector creation flags. */
-#define ED_SECTOR_CSR 1u   /* also build the stored CSR matrix (Fig. 1 layout), FP64 only */
+#define ED_SECTOR_CSR 1u      /* also build the stored CSR matrix (Fig. 1 layout), FP64 only */
+#define ED_SECTOR_GENERIC 2u  /* skip the row-kernel tables: H*v uses the generic kernels only */
 
 typedef struct ed_ctx ed_ctx;
 typedef struct ed_sector ed_sector;
@@ -104,6 +105,7 @@ typedef struct ed_sector_info {
   uint64_t csr_nnz;             /* stored CSR entries (0 without ED_SECTOR_CSR) */
   uint64_t table_bytes;         /* device bytes held by the sector */
   double   nnz_per_row;         /* mean stored entries per row of H (diagonal included) */
+  int      kernel;              /* H*v kernel: 0 flat, 1 row-staged generic, 2 fast row kernel */
 } ed_sector_info;
 
 /* ------------------------------------------------------------------ errors */

@@ -23,6 +23,7 @@ ED_OK, ED_ERR_INVALID, ED_ERR_OOM, ED_ERR_CUDA, ED_ERR_TIMEOUT, ED_ERR_NOT_CONVE
 ED_PREC_FP64, ED_PREC_DF64, ED_PREC_FP32 = 0, 1, 2
 ED_SPIN_UP, ED_SPIN_DN = 0, 1
 ED_SECTOR_CSR = 1
+ED_SECTOR_GENERIC = 2
 ED_MAX_K = 64
 PREC_NAMES = {"fp64": ED_PREC_FP64, "df64": ED_PREC_DF64, "fp32": ED_PREC_FP32}
 STATUS_NAMES = {0: "ED_OK", 1: "ED_ERR_INVALID", 2: "ED_ERR_OOM", 3: "ED_ERR_CUDA", 4: "ED_ERR_TIMEOUT",
@@ -45,7 +46,8 @@ class ed_sector_info(C.Structure):
     _fields_ = [("n_s", C.c_int), ("n_up", C.c_int), ("n_dn", C.c_int), ("prec", C.c_int),
                 ("D_up", C.c_uint64), ("D_dn", C.c_uint64), ("dim", C.c_uint64),
                 ("hops_up", C.c_uint64), ("hops_dn", C.c_uint64), ("mix_up", C.c_uint64),
-                ("csr_nnz", C.c_uint64), ("table_bytes", C.c_uint64), ("nnz_per_row", C.c_double)]
+                ("csr_nnz", C.c_uint64), ("table_bytes", C.c_uint64), ("nnz_per_row", C.c_double),
+                ("kernel", C.c_int)]
 
 
 class ed_lanczos_opts(C.Structure):

@@ -205,9 +205,10 @@ int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn, int
   ED_GUARD_BEGIN
   if (!ctx || !model || !out) ED_INVALID("NULL argument");
   *out = nullptr;
-  if (flags & ~ED_SECTOR_CSR) ED_INVALID("unknown flags 0x%x", flags);
+  if (flags & ~(ED_SECTOR_CSR | ED_SECTOR_GENERIC)) ED_INVALID("unknown flags 0x%x", flags);
   ed_sector* h = new ed_sector();
   int st = build_sector(&ctx->c, model, n_up, n_dn, prec, &h->s);
+  if (st == ED_OK && !(flags & ED_SECTOR_GENERIC)) st = build_fast(&h->s);
   if (st == ED_OK && (flags & ED_SECTOR_CSR)) st = build_csr(&h->s);
   if (st != ED_OK) {
     free_sector(&h->s);
@@ -256,6 +257,7 @@ int ed_sector_get_info(const ed_sector* h, ed_sector_info* out) {
       mix = (double)s.n_mix / s.up.D * (num / den);
     }
   }
+  out->kernel = s.fast.ok ? 2 : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
   out->nnz_per_row = 1.0 + (double)s.dn.n_hops / std::max<uint32_t>(s.dn.D, 1) +
                      (double)s.up.n_hops / std::max<uint32_t>(s.up.D, 1) + mix;
   return ED_OK;

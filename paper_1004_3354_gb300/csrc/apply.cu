@@ -170,6 +170,7 @@ int launch(const Sector* s, const void* xv, void* yv, cudaStream_t st) {
 int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st) {
   if (!x || !y) ED_INVALID("x or y is NULL");
   if (x == y) ED_INVALID("x and y must not overlap");
+  if (s->fast.ok) return apply_fast(s, x, y, st);
   switch (s->prec) {
     case ED_PREC_FP64: return launch<PolF64>(s, x, y, st);
     case ED_PREC_DF64: return launch<PolDF>(s, x, y, st);

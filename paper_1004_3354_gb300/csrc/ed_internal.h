@@ -130,6 +130,23 @@ struct Sector {
   float2* mx_val_df = nullptr;
   uint8_t* mx_mv = nullptr;
   int32_t* dn_move = nullptr;
+  // tables of the fast row kernel (apply_fast.cu); fast.ok = false -> generic kernels
+  struct Fast {
+    bool ok = false;
+    uint32_t max_cnt = 0;       // widest down-hop list
+    int n_coef = 0;             // distinct down-hop matrix elements (<= 256)
+    int n_pat = 1;              // 2^K diagonal patterns
+    uint32_t* perm = nullptr;   // [D_dn] q -> d, sorted by (low-K pattern, hop count, d)
+    uint8_t* cnt = nullptr;     // [D_dn] hop count of perm[q]
+    uint32_t* hop = nullptr;    // [max_cnt][D_dn] (target rank << 8) | coefficient id
+    double* coef = nullptr;     // [n_coef]
+    float2* coef_df = nullptr;
+    double* dd = nullptr;       // [n_pat][D_dn] e_dn[d] + W[p_u][pattern(d)], permuted
+    float2* dd_df = nullptr;
+    int32_t* mv = nullptr;      // [M*M][D_dn] down-move table, permuted
+    uint32_t* row_order = nullptr;  // [D_up] rows grouped by one-body connected component
+    uint32_t* row_pat = nullptr;    // [D_up] low-K pattern of each up string
+  } fast;
   // stored CSR (optional)
   uint64_t csr_nnz = 0;
   uint64_t* csr_ptr = nullptr;
@@ -158,6 +175,10 @@ int validate_model(const ed_model* m);
 int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sector* s);
 int build_csr(Sector* s);
 void free_sector(Sector* s);
+
+// Fast row kernel set-up (apply_fast.cu); leaves fast.ok false when unsupported.
+int build_fast(Sector* s);
+int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st);
 
 // Apply entry points (apply.cu, csr.cu)
 int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st);

@@ -643,7 +643,9 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
   int restarts = 0;
   const double thr = 1e-13;
   int j = 0;
+  bool exhausted = false;
   while (!done) {
+    exhausted = false;
     for (; j < mmax; ++j) {
       V* vj = vec(j);
       V* vjm = (j > 0) ? vec(j - 1) : nullptr;
@@ -668,6 +670,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
       std::memcpy(&ex, ctx->h_red, sizeof(int));
       if (ex >= 0) {
         m = ex;  // T is complete up to here; later steps are discarded
+        exhausted = true;
         ++j;
         break;
       }
@@ -697,7 +700,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
       }
     }
     if (done) break;
-    if (j >= mmax && m >= mmax) {
+    if (!exhausted && j >= mmax && m >= mmax) {
       status = ED_ERR_NOT_CONVERGED;
       break;
     }

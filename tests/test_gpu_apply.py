@@ -38,9 +38,11 @@ def oracle_csr(name, m, nu, nd):
     return _CSR[name]
 
 
-def run_apply(ed, ctx, torch, m, nu, nd, prec, x):
-    sec = ed.ed_sector_create(ctx, m, nu, nd, prec)
+def run_apply(ed, ctx, torch, m, nu, nd, prec, x, flags=0, expect_kernel=None):
+    sec = ed.ed_sector_create(ctx, m, nu, nd, prec, flags)
     try:
+        if expect_kernel is not None:
+            assert ed.ed_sector_get_info(sec).kernel == expect_kernel
         n = len(x)
         xd = to_dev(x, prec, ed, torch)
         yd = empty_vec(n, prec, ed, torch)
@@ -92,41 +94,50 @@ def sample_rows(dim, D_dn, k=2500, seed=3):
     return np.array(sorted(r for r in rows if 0 <= r < dim))
 
 
+# (name, model, n_up, n_dn, kernel chosen by default: 0 flat, 1 row-staged generic, 2 fast rows)
 SAMPLED = [
-    ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6),
-    ("Kanamori N_s=13 (6,7) row-staged", lambda: W.kanamori(13, seed=3), 6, 7),
-    ("Hubbard ring N_s=13 (7,6) row-staged K=13", lambda: W.hubbard_cluster(13, tp=0.1), 7, 6),
+    ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6, 0),
+    ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7, 2),
+    ("AIM N_s=13 (7,6)", lambda: W.aim(13, seed=3), 7, 6, 2),
+    ("Kanamori 2 orbitals N_s=13 (7,7)", lambda: W.kanamori(13, seed=8, n_orb=2), 7, 7, 2),
+    ("Hubbard ring N_s=13 (7,6) K=13", lambda: W.hubbard_cluster(13, tp=0.1), 7, 6, 1),
 ]
 
 
+@pytest.mark.parametrize("generic", [False, True], ids=["default", "generic"])
 @pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
-@pytest.mark.parametrize("name,mk,nu,nd", SAMPLED, ids=[c[0] for c in SAMPLED])
-def test_apply_sampled_rows(env, name, mk, nu, nd, prec):
+@pytest.mark.parametrize("name,mk,nu,nd,kern", SAMPLED, ids=[c[0] for c in SAMPLED])
+def test_apply_sampled_rows(env, name, mk, nu, nd, kern, prec, generic):
     ed, ctx, torch = env
     m = mk()
     D_dn = len(osec.spin_basis(m.n_s, nd))
     dim = len(osec.spin_basis(m.n_s, nu)) * D_dn
     x = W.random_vector(dim, seed=2)
     xin = input_for(prec, x)
-    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x)
+    flags = ed.ED_SECTOR_GENERIC if generic else 0
+    want = (1 if D_dn >= 1024 else 0) if generic else kern
+    if prec == "fp32" and want == 1 and D_dn * 4 > 96 * 1024:
+        want = 0
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, flags, expect_kernel=want)
     rows = sample_rows(dim, D_dn)
     ref = osec.apply_rows(m, nu, nd, rows, xin)
     assert rel_err(y[rows], ref) <= TOL[prec], rel_err(y[rows], ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
 def test_apply_n15_half_filling_sampled(env, prec):
     """The N_s=15 (7,8) sector (dim 41,409,225) in the launch configuration the
-    benchmark times, checked on sampled rows."""
+    benchmark times (fast row kernel), checked on sampled rows."""
     ed, ctx, torch = env
     m = W.kanamori(15, seed=0)
     nu, nd = 7, 8
     dim = 6435 * 6435
     x = W.random_vector(dim, seed=1)
-    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x)
+    xin = input_for(prec, x)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, expect_kernel=2)
     rows = sample_rows(dim, 6435, k=1500)
-    ref = osec.apply_rows(m, nu, nd, rows, x)
-    assert rel_err(y[rows], ref) <= 1e-12
+    ref = osec.apply_rows(m, nu, nd, rows, xin)
+    assert rel_err(y[rows], ref) <= TOL[prec]
 
 
 def test_apply_csr_variant(env):
