@@ -83,16 +83,20 @@ typedef struct ed_sector ed_sector;
  * Eq. 1 (Hubbard): T = -t, U_site = U, n_orb = 0.  Eq. 2 (Anderson impurity):
  * star-shaped T (T_0k = V_k, T_kk = eps_k, T_00 = eps_d), U_site[0] = U,
  * n_orb = 1.  Sec. 4 (Kanamori): T_mm = eps_m - mu, T_kk = eps_k, T_mk = V_mk,
- * U_site[m] = U for m < n_orb, Up = U', J, Jsf = Jph = J'.
- * Requirements: 1 <= n_s <= 31; T exactly symmetric; 0 <= n_orb <= min(n_s, 8);
- * the sites with U_site != 0 and the n_orb orbitals are the lowest sites
- * (any layout works, but the diagonal tables grow with the highest such site).
+ * U_site[m] = U on the orbital sites, Up = U', J, Jsf = Jph = J'.  The sums over
+ * m, m' run over the impurity-orbital sites orb0 .. orb0 + n_orb - 1.
+ * Requirements: 1 <= n_s <= 31; T exactly symmetric; 0 <= n_orb <= 8;
+ * 0 <= orb0 and orb0 + n_orb <= n_s; the orbital sites lie within one aligned
+ * block of 8 sites counted from the lowest site that carries U_site != 0 or an
+ * orbital.  Placing the orbitals on the highest sites makes ascending string
+ * order group strings by impurity occupation (the fast layout).
  */
 typedef struct ed_model {
   int n_s;
   const double* T;       /* n_s * n_s, row-major */
   const double* U_site;  /* n_s */
-  int n_orb;
+  int n_orb;             /* M impurity orbitals ... */
+  int orb0;              /* ... on sites orb0 .. orb0 + M - 1 */
   double Up, J, Jsf, Jph;
 } ed_model;
 

@@ -69,6 +69,7 @@ def hamiltonian_terms(model):
         T_ij c+_is c_js                        for every T_ij != 0, both spins
     On-site Hubbard U (Eq. 1, Eq. 2, Sec. 4):
         U_i n_iu n_id
+    The impurity orbitals m of Sec. 4 are the sites orb0 .. orb0 + n_orb - 1.
     Inter-orbital density-density (Sec. 4, m < m'):
         (Up - J delta_ss') n_ms n_m's'
     Spin-flip and pair-hopping (Sec. 4, every ordered m != m'):
@@ -89,16 +90,17 @@ def hamiltonian_terms(model):
             a, b = mode(i, UP, n), mode(i, DN, n)
             terms.append((model.U_site[i], [(a, True), (a, False), (b, True), (b, False)]))
     M = model.n_orb
-    for m in range(M):
-        for mp in range(m + 1, M):
+    orbs = [model.orb0 + m for m in range(M)]   # impurity orbitals d_m sit on these sites
+    for ia, m in enumerate(orbs):
+        for mp in orbs[ia + 1:]:
             for s in (UP, DN):
                 for sp in (UP, DN):
                     c = model.Up - (model.J if s == sp else 0.0)
                     if c != 0.0:
                         a, b = mode(m, s, n), mode(mp, sp, n)
                         terms.append((c, [(a, True), (a, False), (b, True), (b, False)]))
-    for m in range(M):
-        for mp in range(M):
+    for m in orbs:
+        for mp in orbs:
             if m == mp:
                 continue
             if model.Jsf != 0.0:

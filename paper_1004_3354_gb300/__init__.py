@@ -38,8 +38,8 @@ class EdError(RuntimeError):
 
 class ed_model(C.Structure):
     _fields_ = [("n_s", C.c_int), ("T", C.POINTER(C.c_double)), ("U_site", C.POINTER(C.c_double)),
-                ("n_orb", C.c_int), ("Up", C.c_double), ("J", C.c_double), ("Jsf", C.c_double),
-                ("Jph", C.c_double)]
+                ("n_orb", C.c_int), ("orb0", C.c_int), ("Up", C.c_double), ("J", C.c_double),
+                ("Jsf", C.c_double), ("Jph", C.c_double)]
 
 
 class ed_sector_info(C.Structure):
@@ -141,8 +141,8 @@ class Model:
         self.T = np.ascontiguousarray(m.T, dtype=np.float64)
         self.U = np.ascontiguousarray(m.U_site, dtype=np.float64)
         self.c = ed_model(int(m.n_s), self.T.ctypes.data_as(C.POINTER(C.c_double)),
-                          self.U.ctypes.data_as(C.POINTER(C.c_double)), int(m.n_orb), float(m.Up),
-                          float(m.J), float(m.Jsf), float(m.Jph))
+                          self.U.ctypes.data_as(C.POINTER(C.c_double)), int(m.n_orb),
+                          int(getattr(m, "orb0", 0)), float(m.Up), float(m.J), float(m.Jsf), float(m.Jph))
 
 
 # ---------------------------------------------------------------- context

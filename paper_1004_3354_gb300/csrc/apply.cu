@@ -30,8 +30,8 @@ struct Diag<PolF64> {
                                                uint32_t sd, double eu, double x) {
     double dg = eu + S.e_dn[d];
     for (int c = 0; c < S.n_chunks; ++c) {
-      uint32_t uc = (su >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
-      uint32_t dc = (sd >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
+      uint32_t uc = (su >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
+      uint32_t dc = (sd >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
       dg += S.W[S.w_off[c] + (uc << S.w_bits[c]) + dc];
     }
     acc = fma(dg, x, acc);
@@ -45,8 +45,8 @@ struct DiagDF {
     P::mac(acc, eu, x);
     P::mac(acc, S.e_dn_df[d], x);
     for (int c = 0; c < S.n_chunks; ++c) {
-      uint32_t uc = (su >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
-      uint32_t dc = (sd >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
+      uint32_t uc = (su >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
+      uint32_t dc = (sd >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
       P::mac(acc, S.W_df[S.w_off[c] + (uc << S.w_bits[c]) + dc], x);
     }
   }

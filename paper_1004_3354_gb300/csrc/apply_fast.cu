@@ -34,18 +34,18 @@ constexpr int kList = 128;      // max up hops / mixed entries per row on the fa
 constexpr int kMaxCoef = 256;
 
 struct FastView {
-  uint32_t D_up, D;
+  uint32_t D_up, D, D4;
   const uint32_t* row_order;
   const uint32_t* row_pat;
-  const uint32_t* perm;
-  const uint8_t* cnt;
-  const uint32_t* hop;
+  const uint4* perm4;           // [D4/4] q -> d, four at a time
+  const uint8_t* cnt4;          // [D4/4] widest hop list among four consecutive q
+  const uint4* hop4;            // [max_cnt][D4/4] packed hop words
   const double* coef;
   const float2* coef_df;
   int n_coef;
-  const double* dd;
+  const double* dd;             // [n_pat][D4]
   const float2* dd_df;
-  const int32_t* mv;
+  const int32_t* mv;            // natural-order down-move tables [M*M][D]
   const uint32_t *uh_ptr, *uh_tgt;
   const double* uh_val;
   const float2* uh_val_df;
@@ -56,11 +56,6 @@ struct FastView {
   const float2* mx_val_df;
   const uint8_t* mx_mv;
 };
-
-template <class P>
-__device__ __forceinline__ typename P::C ld_e(const FastView& F, uint32_t u) {
-  return P::ld(F.e_up, F.e_up_df, u);
-}
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -73,6 +68,26 @@ size_t fast_smem(uint32_t D, int n_coef) {
          2 * align16(kList * sizeof(C)) + 2 * align16(kList * sizeof(uint64_t)) + align16(kList * 4);
 }
 
+// four diagonal-table entries for consecutive q (16-byte aligned groups)
+template <class C>
+__device__ __forceinline__ void ld4(const C* p, C (&o)[4]);
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double (&o)[4]) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void ld4<float2>(const float2* p, float2 (&o)[4]) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  o[0] = make_float2(a.x, a.y); o[1] = make_float2(a.z, a.w);
+  o[2] = make_float2(b.x, b.y); o[3] = make_float2(b.z, b.w);
+}
+
+template <class V>
+__device__ __forceinline__ void st_stream(V* p, V v) { __stcs(p, v); }
+
 template <class P, int BS, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typename P::V* __restrict__ x,
                                                         typename P::V* __restrict__ y) {
@@ -80,7 +95,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
   using A = typename P::A;
   using C = typename P::C;
   extern __shared__ __align__(16) unsigned char sm[];
-  const uint32_t D = F.D;
+  const uint32_t D = F.D, G4 = F.D4 >> 2;
   unsigned char* p = sm;
   V* xs = reinterpret_cast<V*>(p);
   p += align16(D * sizeof(V));
@@ -112,9 +127,9 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
       lr[k] = (uint64_t)F.uh_tgt[h0 + k] * D;
       lc[k] = P::ld(F.uh_val, F.uh_val_df, h0 + k);
     }
-    uint32_t m0 = 0, nm = 0;
+    uint32_t nm = 0;
     if (F.mx_ptr) {
-      m0 = F.mx_ptr[u];
+      const uint32_t m0 = F.mx_ptr[u];
       nm = F.mx_ptr[u + 1] - m0;
       for (uint32_t k = threadIdx.x; k < nm; k += BS) {
         mr[k] = (uint64_t)F.mx_tgt[m0 + k] * D;
@@ -128,82 +143,125 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
       pat_s = F.row_pat[u];
     }
     __syncthreads();
-    // pass 1: permuted order -- diagonal (down part + cross), down hops, spin-flip / pair-hop
+    // pass 1, permuted order, four consecutive q per thread: the down part of
+    // the diagonal and the down hops (hop counts equal within a warp)
     {
-      const uint64_t ddoff = (uint64_t)pat_s * D;
-      const int nmx = n_mx_s;
-      for (uint32_t q = threadIdx.x; q < D; q += BS) {
-        const uint32_t d = F.perm[q];
-        A acc = P::zero();
-        P::mac(acc, P::ld(F.dd, F.dd_df, ddoff + q), xs[d]);
-        const int c = F.cnt[q];
-        const uint32_t* hp = F.hop + q;
+      const C* ddr = P::ld_ptr(F.dd, F.dd_df) + (uint64_t)pat_s * F.D4;
+      for (uint32_t g = threadIdx.x; g < G4; g += BS) {
+        const uint4 pp = F.perm4[g];
+        const uint32_t pv[4] = {pp.x, pp.y, pp.z, pp.w};
+        C dg[4];
+        ld4<C>(ddr + 4 * (uint64_t)g, dg);
+        A acc[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          acc[e] = P::zero();
+          P::mac(acc[e], dg[e], xs[pv[e]]);
+        }
+        const int c = F.cnt4[g];
+        const uint4* hp = F.hop4 + g;
         for (int k = 0; k < c; ++k) {
-          const uint32_t e = hp[(uint64_t)k * D];
-          P::mac(acc, cs[e & 255u], xs[e >> 8]);
+          const uint4 w = __ldg(hp + (uint64_t)k * G4);
+          const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) P::mac(acc[e], cs[wv[e] & 255u], xs[wv[e] >> 8]);
         }
-        for (int j = 0; j < nmx; ++j) {
-          const int32_t mvv = F.mv[mm[j] + q];
-          if (mvv >= 0) {
-            C cc = mc[j];
-            if (mvv & 1) cc = P::neg(cc);
-            P::mac(acc, cc, x[mr[j] + (uint32_t)(mvv >> 1)]);
-          }
-        }
-        ys[d] = acc;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (4 * g + e < D) ys[pv[e]] = acc[e];
       }
     }
     __syncthreads();
-    // pass 2: natural order -- up part of the diagonal, up hops, store
+    // pass 2, natural order, four strided elements per thread: the up part of
+    // the diagonal, the up hops, spin-flip / pair-hop, one store
     {
-      const C eu = ld_e<P>(F, u);
-      const int nup = n_up_s;
+      const C eu = P::ld(F.e_up, F.e_up_df, u);
+      const int nup = n_up_s, nmx = n_mx_s;
       V* yr = y + (uint64_t)u * D;
-      for (uint32_t d = threadIdx.x; d < D; d += BS) {
-        A acc = ys[d];
-        P::mac(acc, eu, xs[d]);
-        for (int k = 0; k < nup; ++k) P::mac(acc, lc[k], x[lr[k] + d]);
-        yr[d] = P::out(acc);
+      for (uint32_t d0 = threadIdx.x; d0 < D; d0 += 4 * BS) {
+        uint32_t dv[4];
+        bool ok[4];
+        A acc[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          dv[e] = d0 + e * BS;
+          ok[e] = dv[e] < D;
+          const uint32_t dd = ok[e] ? dv[e] : d0;
+          acc[e] = ys[dd];
+          P::mac(acc[e], eu, xs[dd]);
+        }
+        for (int k = 0; k < nup; ++k) {
+          const C c = lc[k];
+          const V* xk = x + lr[k];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (ok[e]) P::mac(acc[e], c, __ldg(xk + dv[e]));
+        }
+        for (int j = 0; j < nmx; ++j) {
+          const int32_t* mvt = F.mv + mm[j];
+          const V* xm = x + mr[j];
+          const C cj = mc[j];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!ok[e]) continue;
+            const int32_t mvv = __ldg(mvt + dv[e]);
+            if (mvv >= 0) P::mac(acc[e], (mvv & 1) ? P::neg(cj) : cj, __ldg(xm + (uint32_t)(mvv >> 1)));
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (ok[e]) st_stream(yr + dv[e], P::out(acc[e]));
       }
     }
   }
 }
 
-// Permuted per-down-string tables.
-__global__ void k_fast_tables(uint32_t D, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ dbasis,
-                              const uint32_t* __restrict__ dh_ptr, const uint32_t* __restrict__ dh_tgt,
-                              const double* __restrict__ dh_val, const double* __restrict__ coef, int n_coef,
-                              uint32_t max_cnt, uint8_t* __restrict__ cnt, uint32_t* __restrict__ hop,
-                              const double* __restrict__ e_dn, const double* __restrict__ W, int wbits, int n_pat,
-                              double* __restrict__ dd, const int32_t* __restrict__ dn_move, int n_mv,
-                              int32_t* __restrict__ mv) {
+// Permuted per-down-string tables, padded to D4 = 4 * ceil(D / 4) entries.
+__global__ void k_fast_tables(uint32_t D, uint32_t D4, const uint32_t* __restrict__ perm,
+                              const uint32_t* __restrict__ dbasis, const uint32_t* __restrict__ dh_ptr,
+                              const uint32_t* __restrict__ dh_tgt, const double* __restrict__ dh_val,
+                              const double* __restrict__ coef, int n_coef, int zero_id, uint32_t max_cnt,
+                              uint32_t* __restrict__ perm_out, uint8_t* __restrict__ cnt4,
+                              uint32_t* __restrict__ hop, const double* __restrict__ e_dn,
+                              const double* __restrict__ W, int w_lo, int wbits, int n_pat,
+                              double* __restrict__ dd) {
   uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= D) return;
-  uint32_t d = perm[q];
-  uint32_t h0 = dh_ptr[d], c = dh_ptr[d + 1] - h0;
-  cnt[q] = (uint8_t)c;
+  if (q >= D4) return;
+  const bool real = q < D;
+  const uint32_t d = real ? perm[q] : 0u;
+  const uint32_t h0 = dh_ptr[d], c = real ? dh_ptr[d + 1] - h0 : 0u;
+  perm_out[q] = d;
   for (uint32_t k = 0; k < max_cnt; ++k) {
-    uint32_t word = 0;
+    uint32_t word = (uint32_t)zero_id;  // target 0 times a zero coefficient
     if (k < c) {
       double v = dh_val[h0 + k];
       int id = 0;
       while (id < n_coef && coef[id] != v) ++id;
       word = (dh_tgt[h0 + k] << 8) | (uint32_t)(id & 255);
     }
-    hop[(uint64_t)k * D + q] = word;
+    hop[(uint64_t)k * D4 + q] = word;
   }
-  uint32_t pd = (wbits > 0) ? (dbasis[d] & ((1u << wbits) - 1u)) : 0u;
+  // widest list among the four q of this group
+  if ((q & 3u) == 0) {
+    uint32_t c4 = 0;
+    for (uint32_t e = 0; e < 4 && q + e < D; ++e) {
+      const uint32_t de = perm[q + e];
+      c4 = max(c4, dh_ptr[de + 1] - dh_ptr[de]);
+    }
+    cnt4[q >> 2] = (uint8_t)c4;
+  }
+  const uint32_t pd = (wbits > 0) ? ((dbasis[d] >> w_lo) & ((1u << wbits) - 1u)) : 0u;
   for (int pu = 0; pu < n_pat; ++pu) {
-    double v = e_dn[d];
-    if (W) v += W[((uint32_t)pu << wbits) + pd];
-    dd[(uint64_t)pu * D + q] = v;
+    double v = real ? e_dn[d] : 0.0;
+    if (W && real) v += W[((uint32_t)pu << wbits) + pd];
+    dd[(uint64_t)pu * D4 + q] = v;
   }
-  for (int j = 0; j < n_mv; ++j) mv[(uint64_t)j * D + q] = dn_move[(uint64_t)j * D + d];
 }
 
-__global__ void k_row_pat(uint32_t D, const uint32_t* __restrict__ ub, int wbits, uint32_t* __restrict__ pat) {
+__global__ void k_row_pat(uint32_t D, const uint32_t* __restrict__ ub, int w_lo, int wbits,
+                          uint32_t* __restrict__ pat) {
   uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < D) pat[u] = (wbits > 0) ? (ub[u] & ((1u << wbits) - 1u)) : 0u;
+  if (u < D) pat[u] = (wbits > 0) ? ((ub[u] >> w_lo) & ((1u << wbits) - 1u)) : 0u;
 }
 
 __global__ void k_df_copy(const double* __restrict__ a, float2* __restrict__ b, uint64_t n) {
@@ -217,17 +275,18 @@ FastView make_view(const Sector* s) {
   const auto& f = s->fast;
   F.D_up = s->up.D;
   F.D = s->dn.D;
+  F.D4 = (F.D + 3u) & ~3u;
   F.row_order = f.row_order;
   F.row_pat = f.row_pat;
-  F.perm = f.perm;
-  F.cnt = f.cnt;
-  F.hop = f.hop;
+  F.perm4 = reinterpret_cast<const uint4*>(f.perm);
+  F.cnt4 = f.cnt;
+  F.hop4 = reinterpret_cast<const uint4*>(f.hop);
   F.coef = f.coef;
   F.coef_df = f.coef_df;
   F.n_coef = f.n_coef;
   F.dd = f.dd;
   F.dd_df = f.dd_df;
-  F.mv = f.mv;
+  F.mv = s->dn_move;
   F.uh_ptr = s->up.hop_ptr;
   F.uh_tgt = s->up.hop_tgt;
   F.uh_val = s->up.hop_val;
@@ -298,7 +357,7 @@ int build_fast(Sector* s) {
   std::vector<uint32_t> perm(D);
   std::iota(perm.begin(), perm.end(), 0u);
   auto key = [&](uint32_t d) {
-    uint32_t pd = wbits ? (dbas[d] & ((1u << wbits) - 1u)) : 0u;
+    uint32_t pd = wbits ? ((dbas[d] >> s->w_lo) & ((1u << wbits) - 1u)) : 0u;
     return ((uint64_t)pd << 32) | (uint64_t)(dptr[d + 1] - dptr[d]);
   };
   std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
@@ -331,32 +390,42 @@ int build_fast(Sector* s) {
 
   auto& f = s->fast;
   f.max_cnt = s->dn.max_hops;
+  // a zero coefficient pads the hop lists of groups whose four strings differ in length
+  int zero_id = -1;
+  for (size_t i = 0; i < coef.size(); ++i)
+    if (coef[i] == 0.0) zero_id = (int)i;
+  if (zero_id < 0) {
+    if (coef.size() >= (size_t)kMaxCoef) return ED_OK;
+    zero_id = (int)coef.size();
+    coef.push_back(0.0);
+  }
   f.n_coef = (int)coef.size();
   f.n_pat = 1 << wbits;
-  const int n_mv = (s->dn_move ? s->M * s->M : 0);
-  ED_TRY(sector_alloc(s, &f.perm, D));
-  ED_TRY(sector_alloc(s, &f.cnt, D));
-  ED_TRY(sector_alloc(s, &f.hop, (size_t)std::max(1u, f.max_cnt) * D));
+  const uint32_t D4 = (D + 3u) & ~3u;
+  uint32_t* dperm = nullptr;
+  ED_TRY(sector_alloc(s, &dperm, D));
+  ED_TRY(sector_alloc(s, &f.perm, D4));
+  ED_TRY(sector_alloc(s, &f.cnt, D4 / 4));
+  ED_TRY(sector_alloc(s, &f.hop, (size_t)std::max(1u, f.max_cnt) * D4));
   ED_TRY(sector_alloc(s, &f.coef, f.n_coef));
-  ED_TRY(sector_alloc(s, &f.dd, (size_t)f.n_pat * D));
-  if (n_mv) ED_TRY(sector_alloc(s, &f.mv, (size_t)n_mv * D));
+  ED_TRY(sector_alloc(s, &f.dd, (size_t)f.n_pat * D4));
   ED_TRY(sector_alloc(s, &f.row_order, Du));
   ED_TRY(sector_alloc(s, &f.row_pat, Du));
-  ED_TRY_CUDA(cudaMemcpy(f.perm, perm.data(), sizeof(uint32_t) * D, cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(dperm, perm.data(), sizeof(uint32_t) * D, cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.coef, coef.data(), sizeof(double) * f.n_coef, cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.row_order, rorder.data(), sizeof(uint32_t) * Du, cudaMemcpyHostToDevice));
-  k_fast_tables<<<(D + 127) / 128, 128>>>(D, f.perm, s->dn.basis, s->dn.hop_ptr, s->dn.hop_tgt, s->dn.hop_val,
-                                          f.coef, f.n_coef, f.max_cnt, f.cnt, f.hop, s->dn.e,
-                                          (s->n_chunks == 1) ? s->W : nullptr, wbits, f.n_pat, f.dd, s->dn_move,
-                                          n_mv, f.mv);
+  k_fast_tables<<<(D4 + 127) / 128, 128>>>(D, D4, dperm, s->dn.basis, s->dn.hop_ptr, s->dn.hop_tgt,
+                                           s->dn.hop_val, f.coef, f.n_coef, zero_id, f.max_cnt, f.perm, f.cnt,
+                                           f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo, wbits,
+                                           f.n_pat, f.dd);
   ED_LAUNCH_CHECK();
-  k_row_pat<<<(Du + 127) / 128, 128>>>(Du, s->up.basis, wbits, f.row_pat);
+  k_row_pat<<<(Du + 127) / 128, 128>>>(Du, s->up.basis, s->w_lo, wbits, f.row_pat);
   ED_LAUNCH_CHECK();
   if (s->prec != ED_PREC_FP64) {
     ED_TRY(sector_alloc(s, &f.coef_df, f.n_coef));
-    ED_TRY(sector_alloc(s, &f.dd_df, (size_t)f.n_pat * D));
+    ED_TRY(sector_alloc(s, &f.dd_df, (size_t)f.n_pat * D4));
     k_df_copy<<<(f.n_coef + 127) / 128, 128>>>(f.coef, f.coef_df, f.n_coef);
-    k_df_copy<<<(unsigned)(((uint64_t)f.n_pat * D + 255) / 256), 256>>>(f.dd, f.dd_df, (uint64_t)f.n_pat * D);
+    k_df_copy<<<(unsigned)(((uint64_t)f.n_pat * D4 + 255) / 256), 256>>>(f.dd, f.dd_df, (uint64_t)f.n_pat * D4);
     ED_LAUNCH_CHECK();
   }
   ED_TRY_CUDA(cudaDeviceSynchronize());

@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t between(int i, int j) {
 }
 
 struct ModelArgs {
-  int n_s, M;
+  int n_s, M, orb0;
   double UpmJ;            // U' - J (same-spin inter-orbital)
   const double* T;        // device n_s * n_s
 };
@@ -65,8 +65,8 @@ __global__ void k_spin_count(ModelArgs m, int n, uint32_t D, const uint32_t* __r
   double acc = 0.0;
   for (int i = 0; i < m.n_s; ++i)
     if ((s >> i) & 1u) acc += m.T[i * m.n_s + i];
-  for (int a = 0; a < m.M; ++a)
-    for (int b = a + 1; b < m.M; ++b)
+  for (int a = m.orb0; a < m.orb0 + m.M; ++a)
+    for (int b = a + 1; b < m.orb0 + m.M; ++b)
       if (((s >> a) & 1u) && ((s >> b) & 1u)) acc += m.UpmJ;
   e[r] = acc;
   uint32_t c = 0;
@@ -120,9 +120,11 @@ __global__ void k_spin_fill(ModelArgs m, uint32_t D, const uint32_t* __restrict_
 }
 
 // Cross diagonal tables: W_c[a][b] = sum_{i in chunk c} U_i a_i b_i
-//                                    + [c == 0] U' sum_{m != m' < M} a_m b_m'.
-__global__ void k_cross(int n_chunks, int4 bits, uint4 off, const double* __restrict__ U,
-                        int M, double Up, uint32_t total, double* __restrict__ W) {
+//                                    + [c == oc] U' sum_{m != m'} a_m b_m'.
+// Chunk c covers sites w_lo + 8c ...; the M orbitals occupy bits o0 .. o0 + M - 1
+// of chunk oc.
+__global__ void k_cross(int n_chunks, int4 bits, uint4 off, const double* __restrict__ U, int w_lo,
+                        int M, int oc, int o0, double Up, uint32_t total, double* __restrict__ W) {
   uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   int bw[4] = {bits.x, bits.y, bits.z, bits.w};
@@ -133,10 +135,10 @@ __global__ void k_cross(int n_chunks, int4 bits, uint4 off, const double* __rest
   uint32_t a = loc >> bw[c], b = loc & ((1u << bw[c]) - 1u);
   double acc = 0.0;
   for (int i = 0; i < bw[c]; ++i)
-    if (((a >> i) & 1u) && ((b >> i) & 1u)) acc += U[8 * c + i];
-  if (c == 0)
-    for (int x = 0; x < M; ++x)
-      for (int y = 0; y < M; ++y)
+    if (((a >> i) & 1u) && ((b >> i) & 1u)) acc += U[w_lo + 8 * c + i];
+  if (c == oc)
+    for (int x = o0; x < o0 + M; ++x)
+      for (int y = o0; y < o0 + M; ++y)
         if (x != y && ((a >> x) & 1u) && ((b >> y) & 1u)) acc += Up;
   W[idx] = acc;
 }
@@ -147,11 +149,11 @@ __global__ void k_cross(int n_chunks, int4 bits, uint4 off, const double* __rest
 // electron b -> a (column d - b + a), the pair-hop partner moves it a -> b.
 // Matrix element: +J' s_u s_d (the Sec. 4 Hamiltonian's -J' with the two
 // one-body bilinears reordered).
-__global__ void k_mix_count(uint32_t D, int M, int nsf, int nph,
+__global__ void k_mix_count(uint32_t D, int M, int o0, int nsf, int nph,
                             const uint32_t* __restrict__ basis, uint32_t* __restrict__ count) {
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= D) return;
-  uint32_t s = basis[r];
+  uint32_t s = basis[r] >> o0;
   uint32_t c = 0;
   for (int a = 0; a < M; ++a)
     for (int b = 0; b < M; ++b)
@@ -159,7 +161,7 @@ __global__ void k_mix_count(uint32_t D, int M, int nsf, int nph,
   count[r] = c;
 }
 
-__global__ void k_mix_fill(uint32_t D, int M, double Jsf, double Jph,
+__global__ void k_mix_fill(uint32_t D, int M, int o0, double Jsf, double Jph,
                            const uint32_t* __restrict__ basis, const uint32_t* __restrict__ C,
                            const uint32_t* __restrict__ ptr, uint32_t* __restrict__ tgt,
                            double* __restrict__ val, uint8_t* __restrict__ mv) {
@@ -169,9 +171,10 @@ __global__ void k_mix_fill(uint32_t D, int M, double Jsf, double Jph,
   uint32_t o = ptr[r];
   for (int a = 0; a < M; ++a)
     for (int b = 0; b < M; ++b) {
-      if (a == b || !((s >> a) & 1u) || ((s >> b) & 1u)) continue;
-      uint32_t t = rank_of(s ^ (1u << a) ^ (1u << b), C);
-      double su = (__popc(s & between(a, b)) & 1) ? -1.0 : 1.0;
+      const int sa = o0 + a, sb = o0 + b;
+      if (a == b || !((s >> sa) & 1u) || ((s >> sb) & 1u)) continue;
+      uint32_t t = rank_of(s ^ (1u << sa) ^ (1u << sb), C);
+      double su = (__popc(s & between(sa, sb)) & 1) ? -1.0 : 1.0;
       if (Jsf != 0.0) {
         tgt[o] = t;
         val[o] = Jsf * su;
@@ -189,12 +192,12 @@ __global__ void k_mix_fill(uint32_t D, int M, double Jsf, double Jph,
 
 // Down-move tables: entry [x*M + y][d] = rank(d - x + y) << 1 | sign bit when
 // x is occupied and y empty in d, else -1.
-__global__ void k_move(uint32_t D, int M, const uint32_t* __restrict__ basis,
+__global__ void k_move(uint32_t D, int M, int o0, const uint32_t* __restrict__ basis,
                        const uint32_t* __restrict__ C, int32_t* __restrict__ mv) {
   uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (uint64_t)D * M * M) return;
   uint32_t p = (uint32_t)(idx / D), d = (uint32_t)(idx % D);
-  int x = p / M, y = p % M;
+  int x = o0 + (int)(p / M), y = o0 + (int)(p % M);
   uint32_t s = basis[d];
   int32_t out = -1;
   if (x != y && ((s >> x) & 1u) && !((s >> y) & 1u)) {
@@ -293,7 +296,7 @@ int build_spin(Sector* s, const double* dT, int n, SpinTables* sp) {
   ED_TRY(sector_alloc(s, &sp->basis, D));
   ED_TRY(sector_alloc(s, &sp->e, D));
   ED_TRY(sector_alloc(s, &sp->hop_ptr, D + 1));
-  ModelArgs ma{s->n_s, s->M, s->Up - s->J, dT};
+  ModelArgs ma{s->n_s, s->M, s->orb0, s->Up - s->J, dT};
   k_spin_count<<<nblk(D, 128), 128>>>(ma, n, (uint32_t)D, c->d_binom, sp->basis, sp->e, sp->hop_ptr);
   ED_LAUNCH_CHECK();
   std::vector<uint32_t> cnt(D + 1, 0);
@@ -324,6 +327,8 @@ int validate_model(const ed_model* m) {
   if (m->n_s < 1 || m->n_s > ED_MAX_SITES) ED_INVALID("n_s=%d outside 1..%d", m->n_s, ED_MAX_SITES);
   if (m->n_orb < 0 || m->n_orb > ED_MAX_ORB || m->n_orb > m->n_s)
     ED_INVALID("n_orb=%d outside 0..min(n_s, %d)", m->n_orb, ED_MAX_ORB);
+  if (m->orb0 < 0 || m->orb0 + m->n_orb > m->n_s)
+    ED_INVALID("orbital sites %d..%d outside 0..%d", m->orb0, m->orb0 + m->n_orb - 1, m->n_s - 1);
   for (int i = 0; i < m->n_s; ++i)
     for (int j = 0; j < m->n_s; ++j) {
       double a = m->T[i * m->n_s + j], b = m->T[j * m->n_s + i];
@@ -343,6 +348,7 @@ SectorView Sector::view() const {
   v.D_dn = dn.D;
   v.n_s = n_s;
   v.M = M;
+  v.w_lo = w_lo;
   v.n_chunks = n_chunks;
   for (int c = 0; c < 4; ++c) {
     v.w_bits[c] = w_bits[c];
@@ -389,6 +395,7 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
   s->n_dn = n_dn;
   s->prec = prec;
   s->M = m->n_orb;
+  s->orb0 = m->orb0;
   std::memcpy(s->T, m->T, sizeof(double) * m->n_s * m->n_s);
   std::memcpy(s->U_site, m->U_site, sizeof(double) * m->n_s);
   s->Up = m->Up;
@@ -404,12 +411,28 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
   ED_TRY(build_spin(s, dT, n_dn, &s->dn));
   s->dim = (uint64_t)s->up.D * s->dn.D;
 
-  // cross tables over the lowest K sites
-  int K = s->M;
+  // cross tables over the window of sites carrying U_site or an orbital
+  int lo = s->n_s, hi = 0;
+  if (s->M > 0) {
+    lo = s->orb0;
+    hi = s->orb0 + s->M;
+  }
   for (int i = 0; i < s->n_s; ++i)
-    if (s->U_site[i] != 0.0) K = std::max(K, i + 1);
+    if (s->U_site[i] != 0.0) {
+      lo = std::min(lo, i);
+      hi = std::max(hi, i + 1);
+    }
+  int K = hi > lo ? hi - lo : 0;
+  s->w_lo = K ? lo : 0;
   s->K = K;
   s->n_chunks = (K + 7) / 8;
+  int ocnk = 0, obit = 0;
+  if (s->M > 0) {
+    ocnk = (s->orb0 - s->w_lo) / 8;
+    obit = (s->orb0 - s->w_lo) % 8;
+    if ((s->orb0 + s->M - 1 - s->w_lo) / 8 != ocnk)
+      ED_INVALID("impurity orbitals straddle an 8-site block of the interaction window");
+  }
   uint32_t total = 0;
   for (int c = 0; c < s->n_chunks; ++c) {
     s->w_bits[c] = std::min(8, K - 8 * c);
@@ -427,7 +450,7 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
     k_cross<<<nblk(total, 256), 256>>>(s->n_chunks,
                                        make_int4(s->w_bits[0], s->w_bits[1], s->w_bits[2], s->w_bits[3]),
                                        make_uint4(s->w_off[0], s->w_off[1], s->w_off[2], s->w_off[3]),
-                                       dU, s->M, s->Up, total, s->W);
+                                       dU, s->w_lo, s->M, ocnk, obit, s->Up, total, s->W);
     ED_LAUNCH_CHECK();
     if (prec != ED_PREC_FP64) {
       ED_TRY(sector_alloc(s, &s->W_df, total));
@@ -441,7 +464,7 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
   if (s->M >= 2 && (nsf || nph)) {
     uint32_t D = s->up.D;
     ED_TRY(sector_alloc(s, &s->mx_ptr, (size_t)D + 1));
-    k_mix_count<<<nblk(D, 128), 128>>>(D, s->M, nsf, nph, s->up.basis, s->mx_ptr);
+    k_mix_count<<<nblk(D, 128), 128>>>(D, s->M, s->orb0, nsf, nph, s->up.basis, s->mx_ptr);
     ED_LAUNCH_CHECK();
     std::vector<uint32_t> cnt(D + 1, 0);
     ED_TRY_CUDA(cudaMemcpy(cnt.data(), s->mx_ptr, D * sizeof(uint32_t), cudaMemcpyDeviceToHost));
@@ -451,12 +474,12 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
     ED_TRY(sector_alloc(s, &s->mx_tgt, s->n_mix));
     ED_TRY(sector_alloc(s, &s->mx_val, s->n_mix));
     ED_TRY(sector_alloc(s, &s->mx_mv, s->n_mix));
-    k_mix_fill<<<nblk(D, 128), 128>>>(D, s->M, s->Jsf, s->Jph, s->up.basis, ctx->d_binom, s->mx_ptr,
+    k_mix_fill<<<nblk(D, 128), 128>>>(D, s->M, s->orb0, s->Jsf, s->Jph, s->up.basis, ctx->d_binom, s->mx_ptr,
                                       s->mx_tgt, s->mx_val, s->mx_mv);
     ED_LAUNCH_CHECK();
     uint64_t nm = (uint64_t)s->dn.D * s->M * s->M;
     ED_TRY(sector_alloc(s, &s->dn_move, nm));
-    k_move<<<nblk(nm, 256), 256>>>(s->dn.D, s->M, s->dn.basis, ctx->d_binom, s->dn_move);
+    k_move<<<nblk(nm, 256), 256>>>(s->dn.D, s->M, s->orb0, s->dn.basis, ctx->d_binom, s->dn_move);
     ED_LAUNCH_CHECK();
     if (prec != ED_PREC_FP64 && s->n_mix) {
       ED_TRY(sector_alloc(s, &s->mx_val_df, s->n_mix));

@@ -18,8 +18,8 @@ __device__ __forceinline__ double diag_f64(const SectorView& S, uint32_t u, uint
                                            uint32_t sd) {
   double dg = S.e_up[u] + S.e_dn[d];
   for (int c = 0; c < S.n_chunks; ++c) {
-    uint32_t uc = (su >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
-    uint32_t dc = (sd >> (8 * c)) & ((1u << S.w_bits[c]) - 1u);
+    uint32_t uc = (su >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
+    uint32_t dc = (sd >> (S.w_lo + 8 * c)) & ((1u << S.w_bits[c]) - 1u);
     dg += S.W[S.w_off[c] + (uc << S.w_bits[c]) + dc];
   }
   return dg;

@@ -85,8 +85,10 @@ struct SpinTables {
 struct SectorView {
   uint32_t D_up, D_dn;
   int n_s, M;
-  // cross (up x down) diagonal tables over the lowest K sites, split into
-  // chunks of at most 8 sites: W_c[u_c][d_c] at w_off[c] + (u_c << w_bits[c]) + d_c
+  // cross (up x down) diagonal tables over the K sites w_lo .. w_lo + K - 1,
+  // split into chunks of at most 8 sites: u_c = (u >> (w_lo + 8c)) & mask_c,
+  // W_c[u_c][d_c] at w_off[c] + (u_c << w_bits[c]) + d_c
+  int w_lo;
   int n_chunks;
   int w_bits[4];
   uint32_t w_off[4];
@@ -109,7 +111,7 @@ struct SectorView {
 
 struct Sector {
   Ctx* ctx = nullptr;
-  int n_s = 0, n_up = 0, n_dn = 0, prec = 0, M = 0, K = 0;
+  int n_s = 0, n_up = 0, n_dn = 0, prec = 0, M = 0, K = 0, orb0 = 0, w_lo = 0;
   double T[ED_MAX_SITES * ED_MAX_SITES];
   double U_site[ED_MAX_SITES];
   double Up = 0, J = 0, Jsf = 0, Jph = 0;
@@ -271,6 +273,7 @@ struct PolF64 {
   static constexpr int prec = ED_PREC_FP64;
   __device__ static __forceinline__ A zero() { return 0.0; }
   __device__ static __forceinline__ C ld(const double* d, const float2*, size_t k) { return d[k]; }
+  __device__ static __forceinline__ const C* ld_ptr(const double* d, const float2*) { return d; }
   __device__ static __forceinline__ C neg(C c) { return -c; }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { a = fma(c, x, a); }
   __device__ static __forceinline__ V out(A a) { return a; }
@@ -283,6 +286,7 @@ struct PolDF {
   static constexpr int prec = ED_PREC_DF64;
   __device__ static __forceinline__ A zero() { return make_float2(0.f, 0.f); }
   __device__ static __forceinline__ C ld(const double*, const float2* f, size_t k) { return f[k]; }
+  __device__ static __forceinline__ const C* ld_ptr(const double*, const float2* f) { return f; }
   __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac(a, c, x); }
   __device__ static __forceinline__ V out(A a) { return df_norm(a); }
@@ -295,6 +299,7 @@ struct PolF32 {
   static constexpr int prec = ED_PREC_FP32;
   __device__ static __forceinline__ A zero() { return make_float2(0.f, 0.f); }
   __device__ static __forceinline__ C ld(const double*, const float2* f, size_t k) { return f[k]; }
+  __device__ static __forceinline__ const C* ld_ptr(const double*, const float2* f) { return f; }
   __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac1(a, c, x); }
   __device__ static __forceinline__ V out(A a) { return __fadd_rn(a.x, a.y); }

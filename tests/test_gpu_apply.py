@@ -69,6 +69,8 @@ FULL = [
     ("D_up 1 (0,3)", lambda: W.kanamori(8, seed=2), 0, 3),
     ("D_dn 1 (5,8)", lambda: W.kanamori(8, seed=2), 5, 8),
     ("Kanamori 4 orbitals N_s=9 (4,5)", lambda: W.kanamori(9, seed=4, n_orb=4), 4, 5),
+    ("Kanamori impurity on low sites N_s=8 (4,3)", lambda: W.kanamori(8, seed=1, imp_first=True), 4, 3),
+    ("AIM impurity on low site N_s=6 (3,3)", lambda: W.aim(6, seed=0, imp_first=True), 3, 3),
 ]
 
 
@@ -101,6 +103,8 @@ SAMPLED = [
     ("AIM N_s=13 (7,6)", lambda: W.aim(13, seed=3), 7, 6, 2),
     ("Kanamori 2 orbitals N_s=13 (7,7)", lambda: W.kanamori(13, seed=8, n_orb=2), 7, 7, 2),
     ("Hubbard ring N_s=13 (7,6) K=13", lambda: W.hubbard_cluster(13, tp=0.1), 7, 6, 1),
+    ("Kanamori impurity on low sites N_s=13 (6,7)", lambda: W.kanamori(13, seed=3, imp_first=True), 6, 7, 2),
+    ("Kanamori 4 orbitals N_s=14 (7,5)", lambda: W.kanamori(14, seed=5, n_orb=4), 7, 5, 2),
 ]
 
 

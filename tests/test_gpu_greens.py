@@ -29,9 +29,9 @@ def test_c0_ground_state_gf(env, spin, prec):
     w, v = np.linalg.eigh(H.toarray())
     states = [(3, 3, w[0], v[:, 0])]
     beta, nw, depth = 40.0, 1024, 60
-    ref = og.greens_cf(m, states, beta, nw, 0, spin, depth=depth)
+    ref = og.greens_cf(m, states, beta, nw, m.orb0, spin, depth=depth)
     dv = to_dev(v[:, 0], prec, ed, torch)
-    G = ed.ed_greens_cf(ctx, m, prec, [(3, 3, w[0], dv)], beta, nw, orbital=0, spin=spin, depth=depth)
+    G = ed.ed_greens_cf(ctx, m, prec, [(3, 3, w[0], dv)], beta, nw, orbital=m.orb0, spin=spin, depth=depth)
     assert np.max(np.abs(G - ref)) <= 1e-8, np.max(np.abs(G - ref))
     assert np.all(G.imag < 0)
 
@@ -49,8 +49,9 @@ def test_thermal_mix_and_cutoff(env):
             dstates.append((nu, nd, w[i], to_dev(v[:, i], "fp64", ed, torch)))
     beta, nw, depth = 8.0, 256, 80
     for cut in (0.0, 1e-3):
-        ref = og.greens_cf(m, states, beta, nw, 1, 0, depth=depth, boltz_cut=cut)
-        G = ed.ed_greens_cf(ctx, m, "fp64", dstates, beta, nw, orbital=1, spin=0, depth=depth, boltz_cut=cut)
+        ref = og.greens_cf(m, states, beta, nw, m.orb0 + 1, 0, depth=depth, boltz_cut=cut)
+        G = ed.ed_greens_cf(ctx, m, "fp64", dstates, beta, nw, orbital=m.orb0 + 1, spin=0, depth=depth,
+                            boltz_cut=cut)
         assert np.max(np.abs(G - ref)) <= 1e-8
 
 

@@ -16,10 +16,13 @@ which covers the Hubbard cluster of Eq. 1 (T = -t, U_i = U), the single-orbital
 Anderson impurity of Eq. 2 (star-shaped T, U on the impurity only) and the
 three-orbital Kanamori impurity of the Sec. 4 Hamiltonian (Jsf = Jph = J').
 
-Site conventions: site i is bit i of a spin string; impurity orbitals are sites
-0..M-1, bath sites follow, grouped by the orbital they couple to.  The chemical
-potential shifts impurity levels only (Sec. 4 writes eps_m - mu for d levels and
-bare eps_k for the bath).
+Site conventions: site i is bit i of a spin string.  By default the impurity
+orbitals are the highest sites (orb0 = n_s - M .. n_s - 1) and the bath sites
+0 .. n_s - M - 1 are grouped by the orbital they couple to; ``imp_first=True``
+puts the impurity on sites 0..M-1 instead.  With the impurity on the high bits,
+ascending numeric order of the spin strings lists them grouped by impurity
+occupation.  The chemical potential shifts impurity levels only (Sec. 4 writes
+eps_m - mu for d levels and bare eps_k for the bath).
 """
 from __future__ import annotations
 
@@ -40,13 +43,14 @@ class Model:
     n_s: int
     T: np.ndarray            # (n_s, n_s) float64, symmetric
     U_site: np.ndarray       # (n_s,) float64
-    n_orb: int = 0           # M: sites 0..M-1 carry Up/J/Jsf/Jph terms
+    n_orb: int = 0           # M: sites orb0..orb0+M-1 carry Up/J/Jsf/Jph terms
     Up: float = 0.0
     J: float = 0.0
     Jsf: float = 0.0
     Jph: float = 0.0
     name: str = ""
     params: dict = field(default_factory=dict)
+    orb0: int = 0            # first impurity-orbital site
 
     def __post_init__(self):
         self.T = np.ascontiguousarray(np.asarray(self.T, dtype=np.float64))
@@ -75,9 +79,16 @@ def _bath_layout(n_orb: int, n_bath: int) -> list[int]:
     return owner
 
 
+def _sites(n_s: int, n_orb: int, imp_first: bool):
+    """(impurity sites, bath sites) for the two layouts."""
+    if imp_first:
+        return list(range(n_orb)), list(range(n_orb, n_s))
+    return list(range(n_s - n_orb, n_s)), list(range(n_s - n_orb))
+
+
 def aim(n_s: int = 6, seed: int = 0, U: float = 4.0, eps_d: float = 0.0, mu: float = 0.0,
-        eps_range=(-2.0, 2.0), v_range=(0.1, 0.5)) -> Model:
-    """Single-orbital Anderson impurity (Eq. 2): impurity site 0, baths 1..n_s-1.
+        eps_range=(-2.0, 2.0), v_range=(0.1, 0.5), imp_first: bool = False) -> Model:
+    """Single-orbital Anderson impurity (Eq. 2) with n_s - 1 bath levels.
 
     Draw order: eps_k for bath 0..N_b-1, then V_k in the same order.
     """
@@ -85,15 +96,18 @@ def aim(n_s: int = 6, seed: int = 0, U: float = 4.0, eps_d: float = 0.0, mu: flo
     nb = n_s - 1
     eps = rng.uniform(eps_range[0], eps_range[1], nb)
     V = rng.uniform(v_range[0], v_range[1], nb)
+    imp, bath = _sites(n_s, 1, imp_first)
+    d = imp[0]
     T = np.zeros((n_s, n_s))
-    T[0, 0] = eps_d - mu
+    T[d, d] = eps_d - mu
     for k in range(nb):
-        T[1 + k, 1 + k] = eps[k]
-        T[0, 1 + k] = T[1 + k, 0] = V[k]
+        s = bath[k]
+        T[s, s] = eps[k]
+        T[d, s] = T[s, d] = V[k]
     Us = np.zeros(n_s)
-    Us[0] = U
-    return Model(n_s, T, Us, n_orb=1, name=f"aim{n_s}",
-                 params=dict(kind="aim", seed=seed, U=U, eps_d=eps_d, mu=mu,
+    Us[d] = U
+    return Model(n_s, T, Us, n_orb=1, name=f"aim{n_s}", orb0=d,
+                 params=dict(kind="aim", seed=seed, U=U, eps_d=eps_d, mu=mu, imp_first=imp_first,
                              eps_range=list(eps_range), v_range=list(v_range)))
 
 
@@ -105,7 +119,7 @@ def kanamori_half_filling_mu(U: float, Up: float, J: float, n_orb: int) -> float
 def kanamori(n_s: int = 12, seed: int = 0, n_orb: int = 3, U: float = 2.3, J: float = 0.4,
              Up: float | None = None, Jp: float | None = None, eps_m: float = 0.0,
              mu: float | None = None, eps_range=(-1.5, 1.5), v_range=(0.1, 0.4),
-             spin_flip: bool = True, pair_hop: bool = True) -> Model:
+             spin_flip: bool = True, pair_hop: bool = True, imp_first: bool = False) -> Model:
     """Multi-orbital Kanamori impurity of the Sec. 4 Hamiltonian with random baths.
 
     Defaults: U' = U - 2J, J' = J, eps_m = 0, mu at the atom's half-filling point.
@@ -122,20 +136,21 @@ def kanamori(n_s: int = 12, seed: int = 0, n_orb: int = 3, U: float = 2.3, J: fl
     owner = _bath_layout(n_orb, nb)
     eps = rng.uniform(eps_range[0], eps_range[1], nb)
     V = rng.uniform(v_range[0], v_range[1], nb)
+    imp, bath = _sites(n_s, n_orb, imp_first)
     T = np.zeros((n_s, n_s))
     for m in range(n_orb):
-        T[m, m] = eps_m - mu
+        T[imp[m], imp[m]] = eps_m - mu
     for k in range(nb):
-        s = n_orb + k
+        s = bath[k]
         T[s, s] = eps[k]
-        T[owner[k], s] = T[s, owner[k]] = V[k]
+        T[imp[owner[k]], s] = T[s, imp[owner[k]]] = V[k]
     Us = np.zeros(n_s)
-    Us[:n_orb] = U
+    Us[imp] = U
     return Model(n_s, T, Us, n_orb=n_orb, Up=Up, J=J,
                  Jsf=Jp if spin_flip else 0.0, Jph=Jp if pair_hop else 0.0,
-                 name=f"kanamori{n_orb}o{n_s}s",
+                 name=f"kanamori{n_orb}o{n_s}s", orb0=imp[0],
                  params=dict(kind="kanamori", seed=seed, n_orb=n_orb, U=U, J=J, Up=Up, Jp=Jp,
-                             eps_m=eps_m, mu=mu, eps_range=list(eps_range),
+                             eps_m=eps_m, mu=mu, eps_range=list(eps_range), imp_first=imp_first,
                              v_range=list(v_range), spin_flip=spin_flip, pair_hop=pair_hop))
 
 
