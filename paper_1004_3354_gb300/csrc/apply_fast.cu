@@ -8,17 +8,20 @@
 //    components of the up-spin one-body hop graph (strings with equal electron
 //    counts on each bond-connected cluster of sites), so the x rows that the
 //    up hops of concurrently processed rows read stay resident in L2.
-//  * Each block stages one x row in shared memory and runs two passes over it:
-//    pass 1 walks the row in a fixed permutation of the down strings sorted by
-//    (diagonal pattern, hop count), so every warp executes the same number of
-//    down hops and the same spin-flip / pair-hop branches; it accumulates the
-//    down hops, the down part of the diagonal and the spin-flip / pair-hop
-//    terms into a shared-memory accumulator row.  Pass 2 walks the row in
-//    natural order, adds the up-spin part of the diagonal and the up hops
-//    (coalesced reads of neighbouring x rows) and writes y once.
-//  * Down-hop entries are packed 4-byte words (target rank << 8 | coefficient
-//    id) with the distinct matrix elements held in shared memory.
+//  * A block stages one x row in shared memory (cp.async) and its warps sweep
+//    the row in windows of 128 consecutive down strings.  Inside a window the
+//    strings are sorted by hop count and dealt to 32 lanes x 4 slots, so the
+//    lanes of a warp run the same number of down hops per slot, every global
+//    access of the warp stays inside the window's 128 elements, and each thread
+//    keeps its four elements in registers from the diagonal to the store.
+//  * Down-hop entries are packed words (target rank << 8 | coefficient id)
+//    with the distinct matrix elements in shared memory; entries with shorter
+//    lists in a slot are padded with a zero coefficient.
+//  * With the impurity orbitals on the top sites, down strings come in blocks
+//    of equal impurity pattern and a spin-flip / pair-hop move shifts the rank
+//    by a per-pattern constant, read from a small shared table.
 #include <algorithm>
+#include <climits>
 #include <functional>
 #include <map>
 #include <numeric>
@@ -30,22 +33,27 @@ namespace ed {
 
 namespace {
 
-constexpr int kList = 128;      // max up hops / mixed entries per row on the fast path
+constexpr int kList = 64;       // max up hops / mixed entries per row on the fast path
 constexpr int kMaxCoef = 256;
+constexpr int kMaxDelta = 256;  // M*M*2^M entries of the move-shift table
+constexpr int kWin = 128;       // strings per window = 32 lanes x 4 slots
 
 struct FastView {
-  uint32_t D_up, D, D4;
+  uint32_t D_up, D, n_win, max_cnt;
   const uint32_t* row_order;
   const uint32_t* row_pat;
-  const uint4* perm4;           // [D4/4] q -> d, four at a time
-  const uint8_t* cnt4;          // [D4/4] widest hop list among four consecutive q
-  const uint4* hop4;            // [max_cnt][D4/4] packed hop words
+  const uint4* perm4;           // [n_win*32] four entries per lane
+  const uchar4* cnt4;           // [n_win] slot counts
+  const uint4* hop4;            // [n_win][max_cnt][32]
   const double* coef;
   const float2* coef_df;
   int n_coef;
-  const double* dd;             // [n_pat][D4]
+  const double* dd;             // [n_pat][n_win*128]
   const float2* dd_df;
   const int32_t* mv;            // natural-order down-move tables [M*M][D]
+  const uint32_t* dpat4;        // [n_win*32] four impurity patterns per lane (delta layout) or NULL
+  const int32_t* mdelta;        // [M*M][np]
+  int np, n_md;
   const uint32_t *uh_ptr, *uh_tgt;
   const double* uh_val;
   const float2* uh_val_df;
@@ -62,13 +70,12 @@ __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t
 template <class P>
 size_t fast_smem(uint32_t D, int n_coef) {
   using V = typename P::V;
-  using A = typename P::A;
   using C = typename P::C;
-  return align16(D * sizeof(V)) + align16(D * sizeof(A)) + align16(n_coef * sizeof(C)) +
-         2 * align16(kList * sizeof(C)) + 2 * align16(kList * sizeof(uint64_t)) + align16(kList * 4);
+  return align16(D * sizeof(V)) + align16(n_coef * sizeof(C)) + 2 * align16(kList * sizeof(C)) +
+         2 * align16(kList * sizeof(uint64_t)) + align16(kList * 4) + align16(kMaxDelta * 4);
 }
 
-// four diagonal-table entries for consecutive q (16-byte aligned groups)
+// four consecutive table entries (16-byte aligned)
 template <class C>
 __device__ __forceinline__ void ld4(const C* p, C (&o)[4]);
 template <>
@@ -88,19 +95,35 @@ __device__ __forceinline__ void ld4<float2>(const float2* p, float2 (&o)[4]) {
 template <class V>
 __device__ __forceinline__ void st_stream(V* p, V v) { __stcs(p, v); }
 
+// Asynchronous global -> shared copy of one element (cp.async, 4 or 8 bytes).
+template <class V>
+__device__ __forceinline__ void cp_async_elem(V* s, const V* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(sizeof(V)));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t sel4(const uint4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ uint32_t sel4(const uchar4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
 template <class P, int BS, int MINB>
-__global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typename P::V* __restrict__ x,
-                                                        typename P::V* __restrict__ y) {
+__global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typename P::V* __restrict__ x,
+                                                       typename P::V* __restrict__ y) {
   using V = typename P::V;
   using A = typename P::A;
   using C = typename P::C;
   extern __shared__ __align__(16) unsigned char sm[];
-  const uint32_t D = F.D, G4 = F.D4 >> 2;
+  const uint32_t D = F.D;
   unsigned char* p = sm;
   V* xs = reinterpret_cast<V*>(p);
   p += align16(D * sizeof(V));
-  A* ys = reinterpret_cast<A*>(p);
-  p += align16(D * sizeof(A));
   C* cs = reinterpret_cast<C*>(p);
   p += align16(F.n_coef * sizeof(C));
   C* lc = reinterpret_cast<C*>(p);          // up-hop coefficients
@@ -111,17 +134,24 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
   p += align16(kList * sizeof(uint64_t));
   uint64_t* mr = reinterpret_cast<uint64_t*>(p);  // mixed row offsets
   p += align16(kList * sizeof(uint64_t));
-  uint32_t* mm = reinterpret_cast<uint32_t*>(p);  // mixed move-table offsets
+  uint32_t* mm = reinterpret_cast<uint32_t*>(p);  // mixed move offsets
+  p += align16(kList * 4);
+  int32_t* mds = reinterpret_cast<int32_t*>(p);   // move shifts per pattern
   __shared__ int n_up_s, n_mx_s;
   __shared__ uint32_t pat_s;
+  const bool mixd = F.dpat4 != nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NWARP = BS / 32;
+  const uint64_t NE = (uint64_t)F.n_win * kWin;
 
   for (int k = threadIdx.x; k < F.n_coef; k += BS) cs[k] = P::ld(F.coef, F.coef_df, k);
+  for (int k = threadIdx.x; k < F.n_md; k += BS) mds[k] = F.mdelta[k];
 
   for (uint32_t i = blockIdx.x; i < F.D_up; i += gridDim.x) {
     const uint32_t u = F.row_order[i];
     __syncthreads();
     const V* xr = x + (uint64_t)u * D;
-    for (uint32_t d = threadIdx.x; d < D; d += BS) xs[d] = xr[d];
+    for (uint32_t d = threadIdx.x; d < D; d += BS) cp_async_elem(xs + d, xr + d);
     const uint32_t h0 = F.uh_ptr[u], nh = F.uh_ptr[u + 1] - h0;
     for (uint32_t k = threadIdx.x; k < nh; k += BS) {
       lr[k] = (uint64_t)F.uh_tgt[h0 + k] * D;
@@ -134,7 +164,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
       for (uint32_t k = threadIdx.x; k < nm; k += BS) {
         mr[k] = (uint64_t)F.mx_tgt[m0 + k] * D;
         mc[k] = P::ld(F.mx_val, F.mx_val_df, m0 + k);
-        mm[k] = (uint32_t)F.mx_mv[m0 + k] * D;
+        mm[k] = mixd ? (uint32_t)F.mx_mv[m0 + k] * (uint32_t)F.np : (uint32_t)F.mx_mv[m0 + k] * D;
       }
     }
     if (threadIdx.x == 0) {
@@ -142,119 +172,177 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_fast(FastView F, const typen
       n_mx_s = (int)nm;
       pat_s = F.row_pat[u];
     }
+    cp_async_wait_all();
     __syncthreads();
-    // pass 1, permuted order, four consecutive q per thread: the down part of
-    // the diagonal and the down hops (hop counts equal within a warp)
-    {
-      const C* ddr = P::ld_ptr(F.dd, F.dd_df) + (uint64_t)pat_s * F.D4;
-      for (uint32_t g = threadIdx.x; g < G4; g += BS) {
-        const uint4 pp = F.perm4[g];
-        const uint32_t pv[4] = {pp.x, pp.y, pp.z, pp.w};
-        C dg[4];
-        ld4<C>(ddr + 4 * (uint64_t)g, dg);
-        A acc[4];
+
+    const C eu = P::ld(F.e_up, F.e_up_df, u);
+    const int nup = n_up_s, nmx = n_mx_s;
+    const C* ddr = P::ld_ptr(F.dd, F.dd_df) + (uint64_t)pat_s * NE;
+    V* yr = y + (uint64_t)u * D;
+    for (uint32_t w = warp; w < F.n_win; w += NWARP) {
+      const uint32_t ent = w * 32 + lane;   // this lane's four entries
+      const uint4 dq = __ldg(F.perm4 + ent);
+      uint32_t dv[4];
+      bool ok[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          acc[e] = P::zero();
-          P::mac(acc[e], dg[e], xs[pv[e]]);
-        }
-        const int c = F.cnt4[g];
-        const uint4* hp = F.hop4 + g;
-        for (int k = 0; k < c; ++k) {
-          const uint4 w = __ldg(hp + (uint64_t)k * G4);
-          const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) P::mac(acc[e], cs[wv[e] & 255u], xs[wv[e] >> 8]);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (4 * g + e < D) ys[pv[e]] = acc[e];
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t d = sel4(dq, e);
+        ok[e] = d < D;
+        dv[e] = ok[e] ? d : 0u;
       }
-    }
-    __syncthreads();
-    // pass 2, natural order, four strided elements per thread: the up part of
-    // the diagonal, the up hops, spin-flip / pair-hop, one store
-    {
-      const C eu = P::ld(F.e_up, F.e_up_df, u);
-      const int nup = n_up_s, nmx = n_mx_s;
-      V* yr = y + (uint64_t)u * D;
-      for (uint32_t d0 = threadIdx.x; d0 < D; d0 += 4 * BS) {
-        uint32_t dv[4];
-        bool ok[4];
-        A acc[4];
+      C dg[4];
+      ld4<C>(ddr + 4 * (uint64_t)ent, dg);
+      const uchar4 c4 = __ldg(F.cnt4 + w);
+      A acc[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          dv[e] = d0 + e * BS;
-          ok[e] = dv[e] < D;
-          const uint32_t dd = ok[e] ? dv[e] : d0;
-          acc[e] = ys[dd];
-          P::mac(acc[e], eu, xs[dd]);
-        }
-        for (int k = 0; k < nup; ++k) {
-          const C c = lc[k];
-          const V* xk = x + lr[k];
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (ok[e]) P::mac(acc[e], c, __ldg(xk + dv[e]));
-        }
-        for (int j = 0; j < nmx; ++j) {
-          const int32_t* mvt = F.mv + mm[j];
-          const V* xm = x + mr[j];
-          const C cj = mc[j];
+      for (int e = 0; e < 4; ++e) {
+        const V xv = xs[dv[e]];
+        acc[e] = P::zero();
+        P::mac(acc[e], dg[e], xv);
+        P::mac(acc[e], eu, xv);
+      }
+      // down hops (slot 0 holds the longest lists)
+      {
+        const int kmax = c4.x;
+        const uint4* hp = F.hop4 + (uint64_t)w * F.max_cnt * 32 + lane;
+        for (int k = 0; k < kmax; k += 2) {
+          const uint4 h0w = __ldg(hp + (uint64_t)k * 32);
+          const uint4 h1w = (k + 1 < kmax) ? __ldg(hp + (uint64_t)(k + 1) * 32) : make_uint4(0, 0, 0, 0);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            if (!ok[e]) continue;
-            const int32_t mvv = __ldg(mvt + dv[e]);
-            if (mvv >= 0) P::mac(acc[e], (mvv & 1) ? P::neg(cj) : cj, __ldg(xm + (uint32_t)(mvv >> 1)));
+            const int ce = (int)sel4(c4, e);
+            if (k < ce) {
+              const uint32_t wd = sel4(h0w, e);
+              P::mac(acc[e], cs[wd & 255u], xs[wd >> 8]);
+            }
+            if (k + 1 < ce) {
+              const uint32_t wd = sel4(h1w, e);
+              P::mac(acc[e], cs[wd & 255u], xs[wd >> 8]);
+            }
           }
         }
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (ok[e]) st_stream(yr + dv[e], P::out(acc[e]));
       }
+      // up hops, two neighbour rows at a time
+      {
+        int k = 0;
+        for (; k + 1 < nup; k += 2) {
+          const V* x0 = x + lr[k];
+          const V* x1 = x + lr[k + 1];
+          V a0[4], a1[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            a0[e] = __ldg(x0 + dv[e]);
+            a1[e] = __ldg(x1 + dv[e]);
+          }
+          const C c0 = lc[k], c1 = lc[k + 1];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            P::mac(acc[e], c0, a0[e]);
+            P::mac(acc[e], c1, a1[e]);
+          }
+        }
+        if (k < nup) {
+          const V* x0 = x + lr[k];
+          const C c0 = lc[k];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) P::mac(acc[e], c0, __ldg(x0 + dv[e]));
+        }
+      }
+      // spin-flip / pair-hop
+      if (nmx) {
+        if (mixd) {
+          const uint32_t pd4 = __ldg(F.dpat4 + ent);
+          for (int j = 0; j < nmx; ++j) {
+            const V* xm = x + mr[j];
+            const C cj = mc[j];
+            int32_t md[4];
+            V xv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              md[e] = ok[e] ? mds[mm[j] + ((pd4 >> (8 * e)) & 255u)] : INT_MIN;
+              if (md[e] != INT_MIN) xv[e] = __ldg(xm + (int64_t)dv[e] + (md[e] >> 1));
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (md[e] != INT_MIN) P::mac(acc[e], (md[e] & 1) ? P::neg(cj) : cj, xv[e]);
+          }
+        } else {
+          for (int j = 0; j < nmx; ++j) {
+            const int32_t* mvt = F.mv + mm[j];
+            const V* xm = x + mr[j];
+            const C cj = mc[j];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (!ok[e]) continue;
+              const int32_t mvv = __ldg(mvt + dv[e]);
+              if (mvv >= 0) P::mac(acc[e], (mvv & 1) ? P::neg(cj) : cj, __ldg(xm + (uint32_t)(mvv >> 1)));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (ok[e]) st_stream(yr + dv[e], P::out(acc[e]));
     }
   }
 }
 
-// Permuted per-down-string tables, padded to D4 = 4 * ceil(D / 4) entries.
-__global__ void k_fast_tables(uint32_t D, uint32_t D4, const uint32_t* __restrict__ perm,
-                              const uint32_t* __restrict__ dbasis, const uint32_t* __restrict__ dh_ptr,
-                              const uint32_t* __restrict__ dh_tgt, const double* __restrict__ dh_val,
-                              const double* __restrict__ coef, int n_coef, int zero_id, uint32_t max_cnt,
-                              uint32_t* __restrict__ perm_out, uint8_t* __restrict__ cnt4,
-                              uint32_t* __restrict__ hop, const double* __restrict__ e_dn,
-                              const double* __restrict__ W, int w_lo, int wbits, int n_pat,
-                              double* __restrict__ dd) {
-  uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= D4) return;
-  const bool real = q < D;
-  const uint32_t d = real ? perm[q] : 0u;
-  const uint32_t h0 = dh_ptr[d], c = real ? dh_ptr[d + 1] - h0 : 0u;
-  perm_out[q] = d;
+// Window tables: entry idx = w*128 + lane*4 + slot holds down rank perm[idx]
+// (D for padding).  Hop words of entry idx at [w][k][lane][slot].
+__global__ void k_win_tables(uint32_t D, uint32_t n_win, uint32_t max_cnt, const uint32_t* __restrict__ perm,
+                             const uint32_t* __restrict__ dbasis, const uint32_t* __restrict__ dh_ptr,
+                             const uint32_t* __restrict__ dh_tgt, const double* __restrict__ dh_val,
+                             const double* __restrict__ coef, int n_coef, int zero_id,
+                             uint32_t* __restrict__ hop, const double* __restrict__ e_dn,
+                             const double* __restrict__ W, int w_lo, int wbits, int n_pat, double* __restrict__ dd,
+                             int orb0, uint8_t* __restrict__ dpat) {
+  const uint64_t NE = (uint64_t)n_win * kWin;
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NE) return;
+  const uint32_t w = (uint32_t)(idx / kWin), r = (uint32_t)(idx % kWin);  // r = lane*4 + slot
+  const uint32_t d = perm[idx];
+  const bool real = d < D;
+  const uint32_t h0 = real ? dh_ptr[d] : 0u, c = real ? dh_ptr[d + 1] - h0 : 0u;
   for (uint32_t k = 0; k < max_cnt; ++k) {
-    uint32_t word = (uint32_t)zero_id;  // target 0 times a zero coefficient
+    uint32_t word = (uint32_t)zero_id;  // target 0 times the zero coefficient
     if (k < c) {
-      double v = dh_val[h0 + k];
+      const double v = dh_val[h0 + k];
       int id = 0;
       while (id < n_coef && coef[id] != v) ++id;
       word = (dh_tgt[h0 + k] << 8) | (uint32_t)(id & 255);
     }
-    hop[(uint64_t)k * D4 + q] = word;
+    hop[((uint64_t)w * max_cnt + k) * kWin + r] = word;
   }
-  // widest list among the four q of this group
-  if ((q & 3u) == 0) {
-    uint32_t c4 = 0;
-    for (uint32_t e = 0; e < 4 && q + e < D; ++e) {
-      const uint32_t de = perm[q + e];
-      c4 = max(c4, dh_ptr[de + 1] - dh_ptr[de]);
-    }
-    cnt4[q >> 2] = (uint8_t)c4;
-  }
-  const uint32_t pd = (wbits > 0) ? ((dbasis[d] >> w_lo) & ((1u << wbits) - 1u)) : 0u;
+  const uint32_t s = real ? dbasis[d] : 0u;
+  const uint32_t pd = (wbits > 0) ? ((s >> w_lo) & ((1u << wbits) - 1u)) : 0u;
   for (int pu = 0; pu < n_pat; ++pu) {
-    double v = real ? e_dn[d] : 0.0;
-    if (W && real) v += W[((uint32_t)pu << wbits) + pd];
-    dd[(uint64_t)pu * D4 + q] = v;
+    double v = 0.0;
+    if (real) {
+      v = e_dn[d];
+      if (W) v += W[((uint32_t)pu << wbits) + pd];
+    }
+    dd[(uint64_t)pu * NE + idx] = v;
+  }
+  if (dpat) dpat[idx] = (uint8_t)(real ? (s >> orb0) : 0u);
+}
+
+// Rank shift of each impurity move (x -> y) for each pattern p, read off the
+// move table at one string of pattern p (the shift is the same for every
+// string of the pattern when the orbitals are the top sites); INT_MIN where
+// the move does not apply.
+__global__ void k_mix_delta(uint32_t D, const uint32_t* __restrict__ dbasis, const int32_t* __restrict__ mv,
+                            int orb0, int M, int32_t* __restrict__ mdelta) {
+  const int NP = 1 << M;
+  for (int idx = threadIdx.x; idx < M * M * NP; idx += blockDim.x) {
+    const int move = idx / NP, p = idx % NP;
+    int32_t out = INT_MIN;
+    for (uint32_t d = 0; d < D; ++d) {
+      if ((int)(dbasis[d] >> orb0) != p) continue;
+      const int32_t v = mv[(uint64_t)move * D + d];
+      if (v >= 0) out = (int32_t)(((int64_t)(v >> 1) - (int64_t)d) * 2 + (v & 1));
+      break;
+    }
+    mdelta[idx] = out;
   }
 }
 
@@ -275,11 +363,12 @@ FastView make_view(const Sector* s) {
   const auto& f = s->fast;
   F.D_up = s->up.D;
   F.D = s->dn.D;
-  F.D4 = (F.D + 3u) & ~3u;
+  F.n_win = f.n_win;
+  F.max_cnt = f.max_cnt;
   F.row_order = f.row_order;
   F.row_pat = f.row_pat;
   F.perm4 = reinterpret_cast<const uint4*>(f.perm);
-  F.cnt4 = f.cnt;
+  F.cnt4 = reinterpret_cast<const uchar4*>(f.cnt);
   F.hop4 = reinterpret_cast<const uint4*>(f.hop);
   F.coef = f.coef;
   F.coef_df = f.coef_df;
@@ -287,6 +376,10 @@ FastView make_view(const Sector* s) {
   F.dd = f.dd;
   F.dd_df = f.dd_df;
   F.mv = s->dn_move;
+  F.dpat4 = f.mix_delta ? reinterpret_cast<const uint32_t*>(f.dpat) : nullptr;
+  F.mdelta = f.mix_delta ? f.mdelta : nullptr;
+  F.np = 1 << s->M;
+  F.n_md = f.mix_delta ? s->M * s->M * (1 << s->M) : 0;
   F.uh_ptr = s->up.hop_ptr;
   F.uh_tgt = s->up.hop_tgt;
   F.uh_val = s->up.hop_val;
@@ -305,7 +398,7 @@ template <class P, int BS, int MINB>
 int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
   FastView F = make_view<P>(s);
   size_t smem = fast_smem<P>(F.D, F.n_coef);
-  auto kern = k_apply_fast<P, BS, MINB>;
+  auto kern = k_apply_win<P, BS, MINB>;
   ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem));
@@ -318,9 +411,7 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
 
 template <class P>
 int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st) {
-  size_t smem = fast_smem<P>(s->dn.D, s->fast.n_coef);
-  if (smem <= 110 * 1024) return launch_fast<P, 512, 2>(s, x, y, st);
-  return launch_fast<P, 1024, 1>(s, x, y, st);
+  return launch_fast<P, 256, 3>(s, x, y, st);
 }
 
 }  // namespace
@@ -328,10 +419,11 @@ int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st) {
 int build_fast(Sector* s) {
   s->fast.ok = false;
   const uint32_t D = s->dn.D;
-  if (D < 1024 || s->n_chunks > 1 || s->up.max_hops > (uint32_t)kList || s->max_mix > (uint32_t)kList)
+  if (D < 512 || s->n_chunks > 1 || s->up.max_hops > (uint32_t)kList || s->max_mix > (uint32_t)kList)
     return ED_OK;
-  if (s->dn.max_hops > 64 || D >= (1u << 24)) return ED_OK;
-  // distinct down-hop matrix elements
+  if (s->dn.max_hops > 255 || D >= (1u << 24)) return ED_OK;
+  if (s->dn_move && s->M * s->M > kList) return ED_OK;
+  // distinct down-hop matrix elements plus a zero used for padding
   std::vector<double> hv(s->dn.n_hops);
   if (s->dn.n_hops)
     ED_TRY_CUDA(cudaMemcpy(hv.data(), s->dn.hop_val, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost));
@@ -345,22 +437,37 @@ int build_fast(Sector* s) {
         if (coef.size() > (size_t)kMaxCoef) return ED_OK;
       }
   }
-  if (coef.empty()) coef.push_back(0.0);
+  int zero_id = -1;
+  for (size_t i = 0; i < coef.size(); ++i)
+    if (coef[i] == 0.0) zero_id = (int)i;
+  if (zero_id < 0) {
+    if (coef.size() >= (size_t)kMaxCoef) return ED_OK;
+    zero_id = (int)coef.size();
+    coef.push_back(0.0);
+  }
   size_t smem_max = std::max(fast_smem<PolF64>(D, (int)coef.size()), fast_smem<PolDF>(D, (int)coef.size()));
   if (smem_max > 220 * 1024) return ED_OK;
+  const bool mix_delta = s->dn_move && s->orb0 + s->M == s->n_s && s->M * s->M * (1 << s->M) <= kMaxDelta;
 
-  // permutation of the down strings: sort by (diagonal pattern, hop count, rank)
-  const int wbits = (s->n_chunks == 1) ? s->w_bits[0] : 0;
-  std::vector<uint32_t> dbas(D), dptr(D + 1);
-  ED_TRY_CUDA(cudaMemcpy(dbas.data(), s->dn.basis, sizeof(uint32_t) * D, cudaMemcpyDeviceToHost));
+  // window-local order: inside each window of 128 ranks, longest hop list first
+  const uint32_t n_win = (D + kWin - 1) / kWin;
+  std::vector<uint32_t> dptr(D + 1);
   ED_TRY_CUDA(cudaMemcpy(dptr.data(), s->dn.hop_ptr, sizeof(uint32_t) * (D + 1), cudaMemcpyDeviceToHost));
-  std::vector<uint32_t> perm(D);
-  std::iota(perm.begin(), perm.end(), 0u);
-  auto key = [&](uint32_t d) {
-    uint32_t pd = wbits ? ((dbas[d] >> s->w_lo) & ((1u << wbits) - 1u)) : 0u;
-    return ((uint64_t)pd << 32) | (uint64_t)(dptr[d + 1] - dptr[d]);
-  };
-  std::stable_sort(perm.begin(), perm.end(), [&](uint32_t a, uint32_t b) { return key(a) < key(b); });
+  std::vector<uint32_t> perm((size_t)n_win * kWin, D);
+  std::vector<uint8_t> cnt((size_t)n_win * 4, 0);
+  for (uint32_t w = 0; w < n_win; ++w) {
+    std::vector<uint32_t> ds;
+    for (uint32_t d = w * kWin; d < std::min(D, (w + 1) * kWin); ++d) ds.push_back(d);
+    std::stable_sort(ds.begin(), ds.end(), [&](uint32_t a, uint32_t b) {
+      return (dptr[a + 1] - dptr[a]) > (dptr[b + 1] - dptr[b]);
+    });
+    for (size_t r = 0; r < ds.size(); ++r) {
+      const uint32_t slot = (uint32_t)(r / 32), lane = (uint32_t)(r % 32);
+      perm[(size_t)w * kWin + lane * 4 + slot] = ds[r];
+      uint8_t& c = cnt[(size_t)w * 4 + slot];
+      c = (uint8_t)std::max<uint32_t>(c, dptr[ds[r] + 1] - dptr[ds[r]]);
+    }
+  }
 
   // row order: group up strings by electron counts on each bond-connected site cluster
   const int ns = s->n_s;
@@ -389,43 +496,43 @@ int build_fast(Sector* s) {
   std::stable_sort(rorder.begin(), rorder.end(), [&](uint32_t a, uint32_t b) { return rkey[a] < rkey[b]; });
 
   auto& f = s->fast;
-  f.max_cnt = s->dn.max_hops;
-  // a zero coefficient pads the hop lists of groups whose four strings differ in length
-  int zero_id = -1;
-  for (size_t i = 0; i < coef.size(); ++i)
-    if (coef[i] == 0.0) zero_id = (int)i;
-  if (zero_id < 0) {
-    if (coef.size() >= (size_t)kMaxCoef) return ED_OK;
-    zero_id = (int)coef.size();
-    coef.push_back(0.0);
-  }
+  const int wbits = (s->n_chunks == 1) ? s->w_bits[0] : 0;
+  f.n_win = n_win;
+  f.max_cnt = std::max(1u, s->dn.max_hops);
   f.n_coef = (int)coef.size();
   f.n_pat = 1 << wbits;
-  const uint32_t D4 = (D + 3u) & ~3u;
-  uint32_t* dperm = nullptr;
-  ED_TRY(sector_alloc(s, &dperm, D));
-  ED_TRY(sector_alloc(s, &f.perm, D4));
-  ED_TRY(sector_alloc(s, &f.cnt, D4 / 4));
-  ED_TRY(sector_alloc(s, &f.hop, (size_t)std::max(1u, f.max_cnt) * D4));
+  const uint64_t NE = (uint64_t)n_win * kWin;
+  ED_TRY(sector_alloc(s, &f.perm, NE));
+  ED_TRY(sector_alloc(s, &f.cnt, (size_t)n_win * 4));
+  ED_TRY(sector_alloc(s, &f.hop, (size_t)f.max_cnt * NE));
   ED_TRY(sector_alloc(s, &f.coef, f.n_coef));
-  ED_TRY(sector_alloc(s, &f.dd, (size_t)f.n_pat * D4));
+  ED_TRY(sector_alloc(s, &f.dd, (size_t)f.n_pat * NE));
   ED_TRY(sector_alloc(s, &f.row_order, Du));
   ED_TRY(sector_alloc(s, &f.row_pat, Du));
-  ED_TRY_CUDA(cudaMemcpy(dperm, perm.data(), sizeof(uint32_t) * D, cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(f.perm, perm.data(), sizeof(uint32_t) * NE, cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(f.cnt, cnt.data(), cnt.size(), cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.coef, coef.data(), sizeof(double) * f.n_coef, cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.row_order, rorder.data(), sizeof(uint32_t) * Du, cudaMemcpyHostToDevice));
-  k_fast_tables<<<(D4 + 127) / 128, 128>>>(D, D4, dperm, s->dn.basis, s->dn.hop_ptr, s->dn.hop_tgt,
-                                           s->dn.hop_val, f.coef, f.n_coef, zero_id, f.max_cnt, f.perm, f.cnt,
-                                           f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo, wbits,
-                                           f.n_pat, f.dd);
+  f.mix_delta = mix_delta;
+  if (mix_delta) {
+    const int M = s->M, NP = 1 << M;
+    ED_TRY(sector_alloc(s, &f.dpat, NE));
+    ED_TRY(sector_alloc(s, &f.mdelta, (size_t)M * M * NP));
+    k_mix_delta<<<1, 256>>>(D, s->dn.basis, s->dn_move, s->orb0, M, f.mdelta);
+    ED_LAUNCH_CHECK();
+  }
+  k_win_tables<<<(unsigned)((NE + 127) / 128), 128>>>(D, n_win, f.max_cnt, f.perm, s->dn.basis, s->dn.hop_ptr,
+                                                      s->dn.hop_tgt, s->dn.hop_val, f.coef, f.n_coef, zero_id,
+                                                      f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo,
+                                                      wbits, f.n_pat, f.dd, s->orb0, f.dpat);
   ED_LAUNCH_CHECK();
   k_row_pat<<<(Du + 127) / 128, 128>>>(Du, s->up.basis, s->w_lo, wbits, f.row_pat);
   ED_LAUNCH_CHECK();
   if (s->prec != ED_PREC_FP64) {
     ED_TRY(sector_alloc(s, &f.coef_df, f.n_coef));
-    ED_TRY(sector_alloc(s, &f.dd_df, (size_t)f.n_pat * D4));
+    ED_TRY(sector_alloc(s, &f.dd_df, (size_t)f.n_pat * NE));
     k_df_copy<<<(f.n_coef + 127) / 128, 128>>>(f.coef, f.coef_df, f.n_coef);
-    k_df_copy<<<(unsigned)(((uint64_t)f.n_pat * D4 + 255) / 256), 256>>>(f.dd, f.dd_df, (uint64_t)f.n_pat * D4);
+    k_df_copy<<<(unsigned)(((uint64_t)f.n_pat * NE + 255) / 256), 256>>>(f.dd, f.dd_df, (uint64_t)f.n_pat * NE);
     ED_LAUNCH_CHECK();
   }
   ED_TRY_CUDA(cudaDeviceSynchronize());

@@ -134,20 +134,28 @@ struct Sector {
   int32_t* dn_move = nullptr;
   // tables of the fast row kernel (apply_fast.cu); fast.ok = false -> generic kernels
   struct Fast {
+    // Window layout: the down strings are cut into windows of 128 consecutive
+    // ranks; inside a window they are sorted by hop count (longest first) and
+    // dealt to 32 lanes x 4 slots, entry index w*128 + lane*4 + slot.
     bool ok = false;
+    uint32_t n_win = 0;         // ceil(D_dn / 128)
     uint32_t max_cnt = 0;       // widest down-hop list
-    int n_coef = 0;             // distinct down-hop matrix elements (<= 256)
-    int n_pat = 1;              // 2^K diagonal patterns
-    uint32_t* perm = nullptr;   // [D_dn] q -> d, sorted by (low-K pattern, hop count, d)
-    uint8_t* cnt = nullptr;     // [D_dn] hop count of perm[q]
-    uint32_t* hop = nullptr;    // [max_cnt][D_dn] (target rank << 8) | coefficient id
+    int n_coef = 0;             // distinct down-hop matrix elements (<= 256), one of them 0.0
+    int n_pat = 1;              // 2^K diagonal patterns of the up string
+    uint32_t* perm = nullptr;   // [n_win*128] down rank of each entry (D_dn for padding)
+    uint8_t* cnt = nullptr;     // [n_win*4] longest list in each slot
+    uint32_t* hop = nullptr;    // [n_win][max_cnt][32][4] (target rank << 8) | coefficient id
     double* coef = nullptr;     // [n_coef]
     float2* coef_df = nullptr;
-    double* dd = nullptr;       // [n_pat][D_dn] e_dn[d] + W[p_u][pattern(d)], permuted
+    double* dd = nullptr;       // [n_pat][n_win*128] e_dn[d] + W[p_u][pattern(d)]
     float2* dd_df = nullptr;
-    int32_t* mv = nullptr;      // [M*M][D_dn] down-move table, permuted
     uint32_t* row_order = nullptr;  // [D_up] rows grouped by one-body connected component
-    uint32_t* row_pat = nullptr;    // [D_up] low-K pattern of each up string
+    uint32_t* row_pat = nullptr;    // [D_up] diagonal pattern of each up string
+    // orbitals on the top sites: down strings come in blocks of equal impurity
+    // pattern, and an impurity move shifts a rank by a per-pattern constant
+    bool mix_delta = false;
+    uint8_t* dpat = nullptr;        // [n_win*128] impurity pattern of each entry
+    int32_t* mdelta = nullptr;      // [M*M][2^M] (shift << 1 | sign) or INT32_MIN
   } fast;
   // stored CSR (optional)
   uint64_t csr_nnz = 0;

@@ -98,7 +98,7 @@ def sample_rows(dim, D_dn, k=2500, seed=3):
 
 # (name, model, n_up, n_dn, kernel chosen by default: 0 flat, 1 row-staged generic, 2 fast rows)
 SAMPLED = [
-    ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6, 0),
+    ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6, 2),
     ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7, 2),
     ("AIM N_s=13 (7,6)", lambda: W.aim(13, seed=3), 7, 6, 2),
     ("Kanamori 2 orbitals N_s=13 (7,7)", lambda: W.kanamori(13, seed=8, n_orb=2), 7, 7, 2),
