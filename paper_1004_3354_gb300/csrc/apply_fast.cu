@@ -52,6 +52,7 @@ struct FastView {
   const float2* dd_df;
   const int32_t* mv;            // natural-order down-move tables [M*M][D]
   const uint32_t* dpat4;        // [n_win*32] four impurity patterns per lane (delta layout) or NULL
+  const uint32_t* wpat;         // [n_win] impurity pattern shared by the whole window, or ~0u
   const int32_t* mdelta;        // [M*M][np]
   int np, n_md;
   const uint32_t *uh_ptr, *uh_tgt;
@@ -201,26 +202,30 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
         P::mac(acc[e], dg[e], xv);
         P::mac(acc[e], eu, xv);
       }
-      // down hops (slot 0 holds the longest lists)
+      // down hops: slot counts descend (c0 >= c1 >= c2 >= c3), so the first c3
+      // steps serve all four slots, the next c2 - c3 three, and so on
       {
-        const int kmax = c4.x;
         const uint4* hp = F.hop4 + (uint64_t)w * F.max_cnt * 32 + lane;
-        for (int k = 0; k < kmax; k += 2) {
-          const uint4 h0w = __ldg(hp + (uint64_t)k * 32);
-          const uint4 h1w = (k + 1 < kmax) ? __ldg(hp + (uint64_t)(k + 1) * 32) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int ce = (int)sel4(c4, e);
-            if (k < ce) {
-              const uint32_t wd = sel4(h0w, e);
-              P::mac(acc[e], cs[wd & 255u], xs[wd >> 8]);
-            }
-            if (k + 1 < ce) {
-              const uint32_t wd = sel4(h1w, e);
-              P::mac(acc[e], cs[wd & 255u], xs[wd >> 8]);
-            }
-          }
+        const int c0 = c4.x, c1 = c4.y, c2 = c4.z, c3 = c4.w;
+        int k = 0;
+#define ED_HOP(E, WD) P::mac(acc[E], cs[(WD) & 255u], xs[(WD) >> 8])
+        for (; k < c3; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y); ED_HOP(2, h.z); ED_HOP(3, h.w);
         }
+        for (; k < c2; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y); ED_HOP(2, h.z);
+        }
+        for (; k < c1; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y);
+        }
+        for (; k < c0; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x);
+        }
+#undef ED_HOP
       }
       // up hops, two neighbour rows at a time
       {
@@ -250,7 +255,22 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
       }
       // spin-flip / pair-hop
       if (nmx) {
-        if (mixd) {
+        const uint32_t wp = mixd ? F.wpat[w] : 0xffffffffu;
+        if (wp != 0xffffffffu) {
+          // every string of the window has impurity pattern wp: one shift per entry
+          for (int j = 0; j < nmx; ++j) {
+            const int32_t md = mds[mm[j] + wp];
+            if (md == INT_MIN) continue;
+            const V* xm = x + mr[j] + (md >> 1);
+            const C cj = (md & 1) ? P::neg(mc[j]) : mc[j];
+            V xv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) xv[e] = ok[e] ? __ldg(xm + dv[e]) : xs[0];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (ok[e]) P::mac(acc[e], cj, xv[e]);
+          }
+        } else if (mixd) {
           const uint32_t pd4 = __ldg(F.dpat4 + ent);
           for (int j = 0; j < nmx; ++j) {
             const V* xm = x + mr[j];
@@ -377,6 +397,7 @@ FastView make_view(const Sector* s) {
   F.dd_df = f.dd_df;
   F.mv = s->dn_move;
   F.dpat4 = f.mix_delta ? reinterpret_cast<const uint32_t*>(f.dpat) : nullptr;
+  F.wpat = f.mix_delta ? f.wpat : nullptr;
   F.mdelta = f.mix_delta ? f.mdelta : nullptr;
   F.np = 1 << s->M;
   F.n_md = f.mix_delta ? s->M * s->M * (1 << s->M) : 0;
@@ -516,6 +537,16 @@ int build_fast(Sector* s) {
   f.mix_delta = mix_delta;
   if (mix_delta) {
     const int M = s->M, NP = 1 << M;
+    std::vector<uint32_t> dbas(D), wpat(n_win, 0xffffffffu);
+    ED_TRY_CUDA(cudaMemcpy(dbas.data(), s->dn.basis, sizeof(uint32_t) * D, cudaMemcpyDeviceToHost));
+    for (uint32_t w = 0; w < n_win; ++w) {
+      uint32_t p0 = dbas[w * kWin] >> s->orb0;
+      bool same = true;
+      for (uint32_t d = w * kWin; d < std::min(D, (w + 1) * kWin); ++d) same = same && ((dbas[d] >> s->orb0) == p0);
+      if (same) wpat[w] = p0;
+    }
+    ED_TRY(sector_alloc(s, &f.wpat, n_win));
+    ED_TRY_CUDA(cudaMemcpy(f.wpat, wpat.data(), sizeof(uint32_t) * n_win, cudaMemcpyHostToDevice));
     ED_TRY(sector_alloc(s, &f.dpat, NE));
     ED_TRY(sector_alloc(s, &f.mdelta, (size_t)M * M * NP));
     k_mix_delta<<<1, 256>>>(D, s->dn.basis, s->dn_move, s->orb0, M, f.mdelta);

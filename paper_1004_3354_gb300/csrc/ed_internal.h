@@ -155,6 +155,7 @@ struct Sector {
     // pattern, and an impurity move shifts a rank by a per-pattern constant
     bool mix_delta = false;
     uint8_t* dpat = nullptr;        // [n_win*128] impurity pattern of each entry
+    uint32_t* wpat = nullptr;       // [n_win] pattern shared by a whole window, or ~0u
     int32_t* mdelta = nullptr;      // [M*M][2^M] (shift << 1 | sign) or INT32_MIN
   } fast;
   // stored CSR (optional)
