@@ -14,9 +14,10 @@
 //    lanes of a warp run the same number of down hops per slot, every global
 //    access of the warp stays inside the window's 128 elements, and each thread
 //    keeps its four elements in registers from the diagonal to the store.
-//  * Down-hop entries are packed words (target rank << 8 | coefficient id)
-//    with the distinct matrix elements in shared memory; entries with shorter
-//    lists in a slot are padded with a zero coefficient.
+//  * Down-hop entries are packed words holding the shared-memory byte offsets
+//    of the target element (<< 13) and of its matrix element (the distinct
+//    values live in shared memory); shorter lists in a slot are padded with
+//    the zero coefficient.
 //  * With the impurity orbitals on the top sites, down strings come in blocks
 //    of equal impurity pattern and a spin-flip / pair-hop move shifts the rank
 //    by a per-pattern constant, read from a small shared table.
@@ -208,7 +209,9 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
         const uint4* hp = F.hop4 + (uint64_t)w * F.max_cnt * 32 + lane;
         const int c0 = c4.x, c1 = c4.y, c2 = c4.z, c3 = c4.w;
         int k = 0;
-#define ED_HOP(E, WD) P::mac(acc[E], cs[(WD) & 255u], xs[(WD) >> 8])
+#define ED_HOP(E, WD)                                                                     \
+  P::mac(acc[E], *reinterpret_cast<const C*>(reinterpret_cast<const unsigned char*>(cs) + ((WD) & 0x1fffu)), \
+         *reinterpret_cast<const V*>(reinterpret_cast<const unsigned char*>(xs) + ((WD) >> 13)))
         for (; k < c3; ++k) {
           const uint4 h = __ldg(hp + (uint64_t)k * 32);
           ED_HOP(0, h.x); ED_HOP(1, h.y); ED_HOP(2, h.z); ED_HOP(3, h.w);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
 __global__ void k_win_tables(uint32_t D, uint32_t n_win, uint32_t max_cnt, const uint32_t* __restrict__ perm,
                              const uint32_t* __restrict__ dbasis, const uint32_t* __restrict__ dh_ptr,
                              const uint32_t* __restrict__ dh_tgt, const double* __restrict__ dh_val,
-                             const double* __restrict__ coef, int n_coef, int zero_id,
+                             const double* __restrict__ coef, int n_coef, int zero_id, int vbytes, int cbytes,
                              uint32_t* __restrict__ hop, const double* __restrict__ e_dn,
                              const double* __restrict__ W, int w_lo, int wbits, int n_pat, double* __restrict__ dd,
                              int orb0, uint8_t* __restrict__ dpat) {
@@ -324,12 +327,13 @@ __global__ void k_win_tables(uint32_t D, uint32_t n_win, uint32_t max_cnt, const
   const bool real = d < D;
   const uint32_t h0 = real ? dh_ptr[d] : 0u, c = real ? dh_ptr[d + 1] - h0 : 0u;
   for (uint32_t k = 0; k < max_cnt; ++k) {
-    uint32_t word = (uint32_t)zero_id;  // target 0 times the zero coefficient
+    // shared-memory byte offsets: x element << 13 | coefficient
+    uint32_t word = (uint32_t)(zero_id * cbytes);  // element 0 times the zero coefficient
     if (k < c) {
       const double v = dh_val[h0 + k];
       int id = 0;
       while (id < n_coef && coef[id] != v) ++id;
-      word = (dh_tgt[h0 + k] << 8) | (uint32_t)(id & 255);
+      word = ((dh_tgt[h0 + k] * (uint32_t)vbytes) << 13) | (uint32_t)(id * cbytes);
     }
     hop[((uint64_t)w * max_cnt + k) * kWin + r] = word;
   }
@@ -442,7 +446,7 @@ int build_fast(Sector* s) {
   const uint32_t D = s->dn.D;
   if (D < 512 || s->n_chunks > 1 || s->up.max_hops > (uint32_t)kList || s->max_mix > (uint32_t)kList)
     return ED_OK;
-  if (s->dn.max_hops > 255 || D >= (1u << 24)) return ED_OK;
+  if (s->dn.max_hops > 255 || (uint64_t)D * elem_bytes(s->prec) >= (1ull << 19)) return ED_OK;
   if (s->dn_move && s->M * s->M > kList) return ED_OK;
   // distinct down-hop matrix elements plus a zero used for padding
   std::vector<double> hv(s->dn.n_hops);
@@ -554,6 +558,7 @@ int build_fast(Sector* s) {
   }
   k_win_tables<<<(unsigned)((NE + 127) / 128), 128>>>(D, n_win, f.max_cnt, f.perm, s->dn.basis, s->dn.hop_ptr,
                                                       s->dn.hop_tgt, s->dn.hop_val, f.coef, f.n_coef, zero_id,
+                                                      (int)elem_bytes(s->prec), s->prec == ED_PREC_FP64 ? 8 : 8,
                                                       f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo,
                                                       wbits, f.n_pat, f.dd, s->orb0, f.dpat);
   ED_LAUNCH_CHECK();

@@ -144,7 +144,7 @@ struct Sector {
     int n_pat = 1;              // 2^K diagonal patterns of the up string
     uint32_t* perm = nullptr;   // [n_win*128] down rank of each entry (D_dn for padding)
     uint8_t* cnt = nullptr;     // [n_win*4] longest list in each slot
-    uint32_t* hop = nullptr;    // [n_win][max_cnt][32][4] (target rank << 8) | coefficient id
+    uint32_t* hop = nullptr;    // [n_win][max_cnt][32][4] (x byte offset << 13) | coefficient byte offset
     double* coef = nullptr;     // [n_coef]
     float2* coef_df = nullptr;
     double* dd = nullptr;       // [n_pat][n_win*128] e_dn[d] + W[p_u][pattern(d)]
