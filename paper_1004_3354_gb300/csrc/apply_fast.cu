@@ -434,8 +434,11 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
   return ED_OK;
 }
 
+// Three 256-thread blocks per SM for 8-byte elements (shared memory and
+// registers both bound it), four for float rows.
 template <class P>
 int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st) {
+  if (sizeof(typename P::V) == 4) return launch_fast<P, 256, 4>(s, x, y, st);
   return launch_fast<P, 256, 3>(s, x, y, st);
 }
 
