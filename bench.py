@@ -142,15 +142,20 @@ def cpu_baseline(model, x, prec, seconds):
                       f"GB/s = rows/s x {2 * eb} B"}
 
 
-def traffic_for(kernel_src_sha):
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def traffic_for(kernel_src_sha, prec):
+    """DRAM bytes per launch of the row kernel from the committed ncu summary,
+    only if it was captured from the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"k_apply_win_{prec}_n15_traffic.txt")
     try:
-        d = json.load(open(p))
+        kv = dict(line.split(":", 1) for line in open(p) if ":" in line)
     except Exception:
         return None
-    if d.get("apply_src_sha") != kernel_src_sha:
+    if kv.get("apply_src_sha", "").strip() != kernel_src_sha:
         return None
-    return d.get("bytes_per_launch")
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def src_sha():
@@ -298,8 +303,8 @@ def run_ours(a):
         "data": "synthetic (seeded random bath)", "config": workload_config(a.prec, dim),
         "pct_hbm_peak": round(100 * value / world / peak, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic_for(sha),
-                     "kernel": "k_apply_fast", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "frac": round(achieved / peak, 4), "traffic": traffic_for(sha, a.prec),
+                     "kernel": "k_apply_win", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
                      "apply_src_sha": sha},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,

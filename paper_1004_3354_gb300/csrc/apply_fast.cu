@@ -65,6 +65,7 @@ struct FastView {
   const double* mx_val;
   const float2* mx_val_df;
   const uint8_t* mx_mv;
+  double* dotp;                 // optional: per-block partial sums of <x, y>
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
 
   for (int k = threadIdx.x; k < F.n_coef; k += BS) cs[k] = P::ld(F.coef, F.coef_df, k);
   for (int k = threadIdx.x; k < F.n_md; k += BS) mds[k] = F.mdelta[k];
+  A dacc = P::zero();  // <x, y> over this thread's elements (only used with F.dotp)
 
   for (uint32_t i = blockIdx.x; i < F.D_up; i += gridDim.x) {
     const uint32_t u = F.row_order[i];
@@ -305,7 +307,22 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e)
-        if (ok[e]) st_stream(yr + dv[e], P::out(acc[e]));
+        if (ok[e]) {
+          const V yv = P::out(acc[e]);
+          st_stream(yr + dv[e], yv);
+          if (F.dotp) P::dot(dacc, xs[dv[e]], yv);
+        }
+    }
+  }
+  if (F.dotp) {
+    __shared__ A red[BS / 32];
+    dacc = P::warp_sum(dacc);
+    if (lane == 0) red[warp] = dacc;
+    __syncthreads();
+    if (warp == 0) {
+      A v = lane < NWARP ? red[lane] : P::zero();
+      v = P::warp_sum(v);
+      if (lane == 0) F.dotp[blockIdx.x] = P::to_double(v);
     }
   }
 }
@@ -420,8 +437,9 @@ FastView make_view(const Sector* s) {
 }
 
 template <class P, int BS, int MINB>
-int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
+int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
   FastView F = make_view<P>(s);
+  F.dotp = dotp;
   size_t smem = fast_smem<P>(F.D, F.n_coef);
   auto kern = k_apply_win<P, BS, MINB>;
   ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -431,15 +449,16 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
   uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)s->ctx->num_sms * per_sm, F.D_up);
   kern<<<grid, BS, smem, st>>>(F, static_cast<const typename P::V*>(x), static_cast<typename P::V*>(y));
   ED_LAUNCH_CHECK();
+  if (nparts) *nparts = (int)grid;
   return ED_OK;
 }
 
 // Three 256-thread blocks per SM for 8-byte elements (shared memory and
 // registers both bound it), four for float rows.
 template <class P>
-int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st) {
-  if (sizeof(typename P::V) == 4) return launch_fast<P, 256, 4>(s, x, y, st);
-  return launch_fast<P, 256, 3>(s, x, y, st);
+int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+  if (sizeof(typename P::V) == 4) return launch_fast<P, 256, 4>(s, x, y, st, dotp, nparts);
+  return launch_fast<P, 256, 3>(s, x, y, st, dotp, nparts);
 }
 
 }  // namespace
@@ -579,11 +598,11 @@ int build_fast(Sector* s) {
   return ED_OK;
 }
 
-int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st) {
+int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
   switch (s->prec) {
-    case ED_PREC_FP64: return dispatch<PolF64>(s, x, y, st);
-    case ED_PREC_DF64: return dispatch<PolDF>(s, x, y, st);
-    case ED_PREC_FP32: return dispatch<PolF32>(s, x, y, st);
+    case ED_PREC_FP64: return dispatch<PolF64>(s, x, y, st, dotp, nparts);
+    case ED_PREC_DF64: return dispatch<PolDF>(s, x, y, st, dotp, nparts);
+    case ED_PREC_FP32: return dispatch<PolF32>(s, x, y, st, dotp, nparts);
   }
   ED_INVALID("unknown precision");
 }

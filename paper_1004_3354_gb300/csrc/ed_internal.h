@@ -189,7 +189,10 @@ void free_sector(Sector* s);
 
 // Fast row kernel set-up (apply_fast.cu); leaves fast.ok false when unsupported.
 int build_fast(Sector* s);
-int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st);
+// With dotp != NULL the kernel also writes per-block partial sums of <x, Hx>
+// to dotp[0 .. *nparts).
+int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp = nullptr,
+               int* nparts = nullptr);
 
 // Apply entry points (apply.cu, csr.cu)
 int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st);
@@ -286,6 +289,12 @@ struct PolF64 {
   __device__ static __forceinline__ C neg(C c) { return -c; }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { a = fma(c, x, a); }
   __device__ static __forceinline__ V out(A a) { return a; }
+  __device__ static __forceinline__ void dot(A& a, V x, V y) { a = fma(x, y, a); }
+  __device__ static __forceinline__ A warp_sum(A a) {
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+  __device__ static __forceinline__ double to_double(A a) { return a; }
 };
 
 struct PolDF {
@@ -299,6 +308,13 @@ struct PolDF {
   __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac(a, c, x); }
   __device__ static __forceinline__ V out(A a) { return df_norm(a); }
+  __device__ static __forceinline__ void dot(A& a, V x, V y) { df_mac(a, x, y); }
+  __device__ static __forceinline__ A warp_sum(A a) {
+    for (int o = 16; o > 0; o >>= 1)
+      a = df_add(a, make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)));
+    return a;
+  }
+  __device__ static __forceinline__ double to_double(A a) { return (double)a.x + (double)a.y; }
 };
 
 struct PolF32 {
@@ -312,6 +328,13 @@ struct PolF32 {
   __device__ static __forceinline__ C neg(C c) { return make_float2(-c.x, -c.y); }
   __device__ static __forceinline__ void mac(A& a, C c, V x) { df_mac1(a, c, x); }
   __device__ static __forceinline__ V out(A a) { return __fadd_rn(a.x, a.y); }
+  __device__ static __forceinline__ void dot(A& a, V x, V y) { df_mac1(a, make_float2(x, 0.f), y); }
+  __device__ static __forceinline__ A warp_sum(A a) {
+    for (int o = 16; o > 0; o >>= 1)
+      a = df_add(a, make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o)));
+    return a;
+  }
+  __device__ static __forceinline__ double to_double(A a) { return (double)a.x + (double)a.y; }
 };
 
 }  // namespace ed

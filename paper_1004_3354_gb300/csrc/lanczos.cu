@@ -145,9 +145,19 @@ struct Coefs {
   double* scale;    // running max |alpha|, beta
   int* exhausted;   // first step with a vanished beta, -1 if none
   double* out;      // generic scalar output slots
+  // three-vector recurrence on unnormalised vectors q_j (v_j = sigma_j q_j):
+  // q_{j+1} = ua_j H q_j + ub_j q_j + uc_j q_{j-1}
+  double* sigma;
+  double* ua_d;
+  float2* ua_f;
+  double* ub_d;
+  float2* ub_f;
+  double* uc_d;
+  float2* uc_f;
 };
 
-enum FinishOp { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NEGH = 3, OP_NORM_INV = 4 };
+enum FinishOp { OP_SUM = 0, OP_ALPHA = 1, OP_BETA = 2, OP_NEGH = 3, OP_NORM_INV = 4, OP_SIGMA0 = 5,
+                OP_ALPHA_Q = 6, OP_BETA_Q = 7 };
 
 // Sum nb partials (one output per block of this kernel) and apply `op`.
 __global__ void __launch_bounds__(kRedThreads) k_finish(const double* __restrict__ partial, int nb, int op,
@@ -192,6 +202,38 @@ __global__ void __launch_bounds__(kRedThreads) k_finish(const double* __restrict
       c.inv_f[slot] = df_from_double(inv);
       break;
     }
+    case OP_SIGMA0: {  // v = <q_0, q_0>
+      double b = sqrt(fmax(v, 0.0));
+      c.out[0] = b;
+      c.sigma[0] = b > 0.0 ? 1.0 / b : 0.0;
+      c.beta[0] = 0.0;
+      break;
+    }
+    case OP_ALPHA_Q: {  // v = <q_j, H q_j>; alpha_j = sigma_j^2 v
+      const int j = slot;
+      const double sg = c.sigma[j];
+      const double a = sg * sg * v;
+      c.alpha[j] = a;
+      *c.scale = fmax(*c.scale, fabs(a));
+      const double ua = sg, ub = -a * sg, uc = (j > 0) ? -c.beta[j] * c.sigma[j - 1] : 0.0;
+      c.ua_d[j] = ua;
+      c.ua_f[j] = df_from_double(ua);
+      c.ub_d[j] = ub;
+      c.ub_f[j] = df_from_double(ub);
+      c.uc_d[j] = uc;
+      c.uc_f[j] = df_from_double(uc);
+      break;
+    }
+    case OP_BETA_Q: {  // v = |q_{j+1}|^2
+      double b = sqrt(fmax(v, 0.0));
+      double sc = fmax(*c.scale, b);
+      *c.scale = sc;
+      bool dead = !(b > thr * fmax(sc, 1.0));
+      if (dead && *c.exhausted < 0) *c.exhausted = slot;
+      c.beta[slot] = dead ? 0.0 : b;
+      c.sigma[slot] = dead ? 0.0 : 1.0 / b;
+      break;
+    }
   }
 }
 
@@ -207,6 +249,42 @@ __global__ void k_lz_update(V* __restrict__ w, const V* __restrict__ v, const V*
     if (vp) amac(a, c.nbe_d, c.nbe_f, j, vp[i]);
     w[i] = store_v(a, w);
   }
+}
+
+// q_out = ua_j y + ub_j q_j + uc_j q_{j-1} with block partials of |q_out|^2.
+// q_out may be the buffer of q_{j-1} (element-wise in place).
+template <class V>
+__global__ void __launch_bounds__(kRedThreads) k_lz_step(const V* __restrict__ y, const V* __restrict__ qj,
+                                                         const V* qjm, V* qout, uint64_t n, Coefs c, int j,
+                                                         double* __restrict__ partial) {
+  using A = typename AccOf<V>::T;
+  __shared__ A sh[32];
+  A nacc{};
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    typename AccOf<V>::T a{};
+    amac(a, c.ua_d, c.ua_f, j, y[i]);
+    amac(a, c.ub_d, c.ub_f, j, qj[i]);
+    if (qjm) amac(a, c.uc_d, c.uc_f, j, qjm[i]);
+    const V q = store_v(a, qout);
+    qout[i] = q;
+    if (partial) dmac(nacc, q, q);
+  }
+  if (partial) {
+    nacc = block_reduce(nacc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = to_d(nacc);
+  }
+}
+
+// Sq[i*ldS + j] = S[i*ldS + j] * sigma[j] (Ritz coefficients on unnormalised q_j)
+__global__ void k_scale_ritz(const double* __restrict__ S, const double* __restrict__ sigma, int m, int k, int ldS,
+                             double* __restrict__ Sq, float2* __restrict__ Sqf) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * k) return;
+  int i = t / m, j = t % m;
+  double v = S[(size_t)i * ldS + j] * sigma[j];
+  Sq[(size_t)i * ldS + j] = v;
+  Sqf[(size_t)i * ldS + j] = df_from_double(v);
 }
 
 // w -= sum_k h_k V_k for k in [0, nvec)
@@ -514,7 +592,7 @@ struct Carve {
 
 size_t coef_bytes(int mmax, int k) {
   size_t m2 = (size_t)mmax + 2;
-  return 256 * 64 + m2 * 8 * 16 + (size_t)k * m2 * 8 * 8 + 2048;
+  return 256 * 64 + m2 * 8 * 24 + (size_t)k * m2 * 8 * 10 + 4096;
 }
 
 Coefs carve_coefs(Carve& cv, int mmax) {
@@ -533,6 +611,13 @@ Coefs carve_coefs(Carve& cv, int mmax) {
   c.scale = cv.take<double>(1);
   c.exhausted = cv.take<int>(1);
   c.out = cv.take<double>(64);
+  c.sigma = cv.take<double>(m2);
+  c.ua_d = cv.take<double>(m2);
+  c.ua_f = cv.take<float2>(m2);
+  c.ub_d = cv.take<double>(m2);
+  c.ub_f = cv.take<float2>(m2);
+  c.uc_d = cv.take<double>(m2);
+  c.uc_f = cv.take<float2>(m2);
   return c;
 }
 
@@ -548,6 +633,9 @@ __global__ void k_init_coefs(Coefs c, int m2) {
     c.inv_f[i] = make_float2(0, 0);
     c.h_d[i] = 0;
     c.h_f[i] = make_float2(0, 0);
+    c.sigma[i] = 0;
+    c.ua_d[i] = c.ub_d[i] = c.uc_d[i] = 0;
+    c.ua_f[i] = c.ub_f[i] = c.uc_f[i] = make_float2(0, 0);
   }
   if (threadIdx.x == 0) {
     *c.scale = 0.0;
@@ -783,6 +871,49 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
   return status;
 }
 
+// Three-vector recurrence on unnormalised vectors (v_j = sigma_j q_j), two
+// large kernels per step: H q_j fused with <q_j, H q_j>, then the update fused
+// with |q_{j+1}|^2.  The coefficients stay on the device.
+template <class V>
+struct Rec3 {
+  Sector* s;
+  Work<V>* W;
+  V* Q[3];  // q_{j-1}, q_j, q_{j+1} rotate through these
+  V* Y;     // H q_j
+  uint32_t sgrid;
+  V* q(int j) { return Q[((j % 3) + 3) % 3]; }
+
+  int apply_dot(const V* x, V* y, int* np) {
+    if (s->fast.ok) return apply_fast(s, x, y, W->st, W->partial, np);
+    ED_TRY(apply_h(s, x, y, W->st));
+    k_dot<V><<<W->grid, kRedThreads, 0, W->st>>>(x, y, W->n, W->partial);
+    ED_LAUNCH_CHECK();
+    *np = (int)W->grid;
+    return ED_OK;
+  }
+  int init() {  // q_0 already in Q[0]
+    return dot_to(*W, (const V*)q(0), (const V*)q(0), OP_SIGMA0, 0);
+  }
+  int step(int j, double thr) {
+    int np = 0;
+    ED_TRY(apply_dot(q(j), Y, &np));
+    k_finish<<<1, kRedThreads, 0, W->st>>>(W->partial, np, OP_ALPHA_Q, j, W->c, 0.0);
+    k_lz_step<V><<<sgrid, kRedThreads, 0, W->st>>>(Y, q(j), j > 0 ? q(j - 1) : nullptr, q(j + 1), W->n, W->c, j,
+                                                   W->partial);
+    k_finish<<<1, kRedThreads, 0, W->st>>>(W->partial, (int)sgrid, OP_BETA_Q, j + 1, W->c, thr);
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+  }
+  // Regenerate q_{j+1} from q_j, q_{j-1} with the stored coefficients.
+  int regen(int j) {
+    ED_TRY(apply_h(s, q(j), Y, W->st));
+    k_lz_step<V><<<sgrid, kRedThreads, 0, W->st>>>(Y, q(j), j > 0 ? q(j - 1) : nullptr, q(j + 1), W->n, W->c, j,
+                                                   nullptr);
+    ED_LAUNCH_CHECK();
+    return ED_OK;
+  }
+};
+
 template <class V>
 int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, double* b, int* L,
                 cudaStream_t st) {
@@ -793,7 +924,6 @@ int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, do
   ED_TRY(vb.alloc(ctx, 4 * n * eb));
   ED_TRY(cb.alloc(ctx, coef_bytes(depth, 1)));
   V* vecs = static_cast<V*>(vb.p);
-  V* w = vecs + 3 * n;
   Carve cv{static_cast<char*>(cb.p)};
   Coefs c = carve_coefs(cv, depth);
   Work<V> W;
@@ -804,25 +934,12 @@ int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, do
   if (W.grid == 0) W.grid = 1;
   W.partial = ctx->d_red;
   W.c = c;
-  uint32_t vgrid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 16);
-  if (vgrid == 0) vgrid = 1;
+  Rec3<V> R{s, &W, {vecs, vecs + n, vecs + 2 * n}, vecs + 3 * n, W.grid};
   k_init_coefs<<<1, 256, 0, st>>>(c, depth + 2);
-  const V* ph = static_cast<const V*>(phi);
-  ED_TRY(dot_to(W, ph, ph, OP_NORM_INV, 0));
-  k_scale<V><<<vgrid, 256, 0, st>>>(ph, vecs, n, c, 0);
-  ED_LAUNCH_CHECK();
+  ED_TRY_CUDA(cudaMemcpyAsync(R.q(0), phi, n * eb, cudaMemcpyDeviceToDevice, st));
+  ED_TRY(R.init());
   const double thr = 1e-12;
-  for (int j = 0; j < depth; ++j) {
-    V* vj = vecs + (size_t)(j % 3) * n;
-    V* vjm = j > 0 ? vecs + (size_t)((j + 2) % 3) * n : nullptr;
-    ED_TRY(apply_h(s, vj, w, st));
-    ED_TRY(dot_to(W, (const V*)vj, (const V*)w, OP_ALPHA, j));
-    if (j + 1 == depth) break;
-    k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vj, vjm, n, c, j);
-    ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_BETA, j + 1, thr));
-    k_scale<V><<<vgrid, 256, 0, st>>>(w, vecs + (size_t)((j + 1) % 3) * n, n, c, j + 1);
-    ED_LAUNCH_CHECK();
-  }
+  for (int j = 0; j < depth; ++j) ED_TRY(R.step(j, thr));
   std::vector<double> hb(depth + 1), ha(depth);
   double norm = 0.0;
   int ex = -1;
@@ -832,7 +949,7 @@ int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, do
   ED_TRY_CUDA(cudaMemcpyAsync(&ex, c.exhausted, sizeof(int), cudaMemcpyDeviceToHost, st));
   ED_TRY_CUDA(cudaStreamSynchronize(st));
   *n2 = norm * norm;
-  int len = (ex >= 0) ? ex : depth;
+  int len = (ex >= 0 && ex < depth) ? ex : depth;
   if (norm == 0.0) len = 0;
   *L = len;
   for (int i = 0; i < depth; ++i) {
@@ -840,6 +957,118 @@ int coeffs_impl(Sector* s, const void* phi, int depth, double* n2, double* a, do
     b[i] = (i < len && i > 0) ? hb[i] : 0.0;
   }
   return ED_OK;
+}
+
+// Lanczos without reorthogonalisation: three resident vectors, eigenvalues from
+// the tridiagonal matrix, Ritz vectors by a second pass that regenerates the
+// same q_j with the stored coefficients.
+template <class V>
+int lanczos3_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
+                  cudaStream_t st) {
+  auto t_start = std::chrono::steady_clock::now();
+  Ctx* ctx = s->ctx;
+  const uint64_t n = s->dim;
+  const int k = o->k;
+  int mmax = (int)std::min<uint64_t>((uint64_t)o->max_iter, n);
+  if (mmax < 1) mmax = 1;
+  const int check_every = std::max(1, o->check_every);
+  const int kk = std::min<int>(k, (int)n);
+  size_t eb = sizeof(V);
+  DevBuf vb, cb, v0b;
+  ED_TRY(vb.alloc(ctx, 4 * n * eb));
+  ED_TRY(v0b.alloc(ctx, n * eb));
+  ED_TRY(cb.alloc(ctx, coef_bytes(mmax, std::max(kk, 1))));
+  V* vecs = static_cast<V*>(vb.p);
+  Carve cv{static_cast<char*>(cb.p)};
+  Coefs c = carve_coefs(cv, mmax);
+  int ldS = mmax + 1;
+  double* theta = cv.take<double>(ED_MAX_K);
+  double* resid = cv.take<double>(ED_MAX_K);
+  double* Sd = cv.take<double>((size_t)ldS * std::max(kk, 1));
+  float2* Sf = cv.take<float2>((size_t)ldS * std::max(kk, 1));
+  double* Sq = cv.take<double>((size_t)ldS * std::max(kk, 1));
+  float2* Sqf = cv.take<float2>((size_t)ldS * std::max(kk, 1));
+  double* twork = cv.take<double>((size_t)6 * ldS * std::max(kk, 1));
+  Work<V> W;
+  W.ctx = ctx;
+  W.st = st;
+  W.n = n;
+  W.grid = (uint32_t)std::min<uint64_t>((n + kRedThreads - 1) / kRedThreads, (uint64_t)ctx->num_sms * 8);
+  if (W.grid == 0) W.grid = 1;
+  W.partial = ctx->d_red;
+  W.c = c;
+  uint32_t vgrid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 16);
+  if (vgrid == 0) vgrid = 1;
+  Rec3<V> R{s, &W, {vecs, vecs + n, vecs + 2 * n}, vecs + 3 * n, W.grid};
+  k_init_coefs<<<1, 256, 0, st>>>(c, mmax + 2);
+  if (o->v0) {
+    ED_TRY_CUDA(cudaMemcpyAsync(R.q(0), o->v0, n * eb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    k_random<V><<<vgrid, 256, 0, st>>>(R.q(0), n, o->seed);
+  }
+  ED_TRY_CUDA(cudaMemcpyAsync(v0b.p, R.q(0), n * eb, cudaMemcpyDeviceToDevice, st));
+  ED_TRY(R.init());
+  std::vector<double> h_theta(ED_MAX_K), h_res(ED_MAX_K);
+  int m = 0, n_conv = 0, status = ED_OK;
+  const double thr = 1e-13;
+  for (int j = 0; j < mmax; ++j) {
+    ED_TRY(R.step(j, thr));
+    m = j + 1;
+    bool check = ((m % check_every) == 0) || (m == mmax) || (n <= 4096);
+    if (!check) continue;
+    int ex = -1;
+    ED_TRY_CUDA(cudaMemcpyAsync(ctx->h_red, c.exhausted, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ED_TRY_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(&ex, ctx->h_red, sizeof(int));
+    bool exhausted = ex >= 0;
+    if (exhausted) m = ex;
+    int kc = std::min(kk, m);
+    ED_TRY(tridiag(ctx, st, c, m, kc, 0.0, theta, Sd, Sf, ldS, resid, twork));
+    std::vector<double> last(kc);
+    double bm = 0.0;
+    ED_TRY_CUDA(cudaMemcpyAsync(&bm, c.beta + m, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ED_TRY_CUDA(cudaMemcpyAsync(h_theta.data(), theta, kc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < kc; ++i)
+      ED_TRY_CUDA(cudaMemcpyAsync(&last[i], Sd + (size_t)i * ldS + m - 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ED_TRY_CUDA(cudaStreamSynchronize(st));
+    if (exhausted) bm = 0.0;
+    n_conv = 0;
+    for (int i = 0; i < kc; ++i) {
+      h_res[i] = std::fabs(bm * last[i]);
+      if (h_res[i] <= o->tol * std::max(1.0, std::fabs(h_theta[i])) && n_conv == i) ++n_conv;
+    }
+    if (exhausted || (kc >= kk && n_conv >= kk)) break;
+    if (m >= mmax) status = ED_ERR_NOT_CONVERGED;
+  }
+  if (m >= mmax && n_conv < kk) status = ED_ERR_NOT_CONVERGED;
+  int kc = std::min(kk, m);
+  for (int i = 0; i < kc; ++i) evals[i] = h_theta[i];
+  for (int i = kc; i < k; ++i) evals[i] = NAN;
+  if (info) {
+    info->iters = m;
+    info->n_converged = std::min(n_conv, kc);
+    for (int i = 0; i < ED_MAX_K; ++i) info->residual[i] = (i < kc) ? h_res[i] : 0.0;
+  }
+  if (evecs && kc > 0) {
+    ED_TRY(tridiag(ctx, st, c, m, kc, 0.0, theta, Sd, Sf, ldS, resid, twork));
+    k_scale_ritz<<<(m * kc + 127) / 128, 128, 0, st>>>(Sd, c.sigma, m, kc, ldS, Sq, Sqf);
+    V* out = static_cast<V*>(evecs);
+    ED_TRY_CUDA(cudaMemsetAsync(out, 0, (size_t)kc * n * eb, st));
+    ED_TRY_CUDA(cudaMemcpyAsync(R.q(0), v0b.p, n * eb, cudaMemcpyDeviceToDevice, st));
+    for (int jj = 0; jj < m; ++jj) {
+      for (int i0 = 0; i0 < kc; i0 += 8)
+        k_ritz<V, 8><<<vgrid, 256, 0, st>>>(R.q(jj), n, 1, Sq + jj, Sqf + jj, ldS, i0, std::min(8, kc - i0), out, n, 1);
+      if (jj + 1 == m) break;
+      ED_TRY(R.regen(jj));
+    }
+    ED_LAUNCH_CHECK();
+  }
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
+  if (info)
+    info->total_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  if (status != ED_OK) set_error("Lanczos did not converge in %d steps", mmax);
+  return status;
 }
 
 }  // namespace
@@ -868,6 +1097,13 @@ int dot_async(Ctx* c, const void* x, const void* y, uint64_t n, int prec, double
 
 int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
                 cudaStream_t st) {
+  if (!o->reorth) {
+    switch (s->prec) {
+      case ED_PREC_FP64: return lanczos3_impl<double>(s, o, evals, evecs, info, st);
+      case ED_PREC_DF64: return lanczos3_impl<float2>(s, o, evals, evecs, info, st);
+      case ED_PREC_FP32: return lanczos3_impl<float>(s, o, evals, evecs, info, st);
+    }
+  }
   switch (s->prec) {
     case ED_PREC_FP64: return lanczos_impl<double>(s, o, evals, evecs, info, st);
     case ED_PREC_DF64: return lanczos_impl<float2>(s, o, evals, evecs, info, st);

@@ -138,3 +138,45 @@ def test_without_reorthogonalisation_ground_state(env):
         assert abs(abs(vv @ refv[:, 0]) - 1.0) <= 1e-9
     finally:
         ed.ed_sector_destroy(sec)
+
+
+_C1 = {}
+
+
+def c1_reference():
+    if not _C1:
+        m = W.kanamori(12, seed=0)
+        H = osec.build_csr(m, 6, 6)
+        w, v = spectrum.lowest(H, 1, vectors=True)
+        _C1.update(m=m, H=H, e0=w[0], v0=v[:, 0])
+    return _C1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_c1_ground_state_three_vectors(env, prec):
+    """C1 ground state with three resident vectors (fused H*v + <q, Hq>, fused
+    update + norm) and the regenerated Ritz vector."""
+    ed, ctx, torch = env
+    r = c1_reference()
+    sec = ed.ed_sector_create(ctx, r["m"], 6, 6, prec)
+    try:
+        n = r["H"].shape[0]
+        v = empty_vec(n, prec, ed, torch)
+        ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-11, max_iter=400, reorth=False, evecs=v)
+        assert abs(ev[0] - r["e0"]) <= 1e-10 * abs(r["e0"]), (ev[0], r["e0"])
+        vv = to_host(v, prec, n, ed, torch)
+        assert abs(abs(vv @ r["v0"]) - 1.0) <= 1e-8
+    finally:
+        ed.ed_sector_destroy(sec)
+
+
+def test_c1_fp32_vectors_ground_energy(env):
+    """FP32 Lanczos vectors, double-float products: ground energy within 1e-6 relative."""
+    ed, ctx, torch = env
+    r = c1_reference()
+    sec = ed.ed_sector_create(ctx, r["m"], 6, 6, "fp32")
+    try:
+        ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-7, max_iter=400, reorth=False, allow_not_converged=True)
+        assert abs(ev[0] - r["e0"]) <= 1e-6 * abs(r["e0"]), (ev[0], r["e0"])
+    finally:
+        ed.ed_sector_destroy(sec)
