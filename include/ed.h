@@ -172,6 +172,23 @@ int ed_convert(const void* src, int src_prec, void* dst, int dst_prec, uint64_t 
  * accumulated in double; the result is written to host memory (synchronises). */
 int ed_dot(ed_ctx* ctx, const void* x, const void* y, uint64_t n, int prec, double* result, void* stream);
 
+/* Allocation-free dot product: the same <x, y> as ed_dot (accumulated in double
+ * for FP64 vectors, in double-float for DF64 and FP32 vectors, the result
+ * written to host memory after synchronising `stream`), for callers that cannot
+ * allocate device memory: a host framework that owns every device allocation,
+ * a process that must not grow its footprint in the middle of a solve, or code
+ * that has no ed_ctx (creating one allocates).  The paper has no counterpart of
+ * this call.  Its partial sums live in one fixed 512 KB __device__ array that
+ * every GPU loading the library keeps until the process exits; n is limited to
+ * 268,435,456 elements (65,536 tiles of 4,096) and a larger n is rejected with
+ * ED_ERR_INVALID before any device work.  It calls no cudaMalloc or cudaFree.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the one array and each call
+ * overwrites it, so calls that overlap on the GPU (other streams or threads)
+ * race and must be serialised by the caller. */
+int ed_dot_noalloc(const void* x, const void* y, uint64_t n, int prec, double* result, void* stream);
+
 /* ----------------------------------------------------------------- Lanczos */
 typedef struct ed_lanczos_opts {
   int k;               /* number of lowest eigenpairs wanted (1..ED_MAX_K) */

@@ -84,6 +84,7 @@ _SIGS = {
     "ed_convert": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     "ed_dot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double),
                          C.c_void_p]),
+    "ed_dot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ed_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                              C.POINTER(ed_lanczos_info), C.c_void_p]),
     "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
@@ -229,6 +230,13 @@ def ed_convert(src, src_prec, dst, dst_prec, n: int, stream=None):
 def ed_dot(ctx, x, y, n: int, prec, stream=None) -> float:
     r = C.c_double()
     check(lib().ed_dot(ctx, _ptr(x), _ptr(y), n, PREC_NAMES.get(prec, prec), C.byref(r), _stream(stream)))
+    return r.value
+
+
+def ed_dot_noalloc(x, y, n: int, prec, stream=None) -> float:
+    """<x, y> without any device allocation (fixed static scratch; see include/ed.h)."""
+    r = C.c_double()
+    check(lib().ed_dot_noalloc(_ptr(x), _ptr(y), n, PREC_NAMES.get(prec, prec), C.byref(r), _stream(stream)))
     return r.value
 
 
