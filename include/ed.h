@@ -237,6 +237,34 @@ int ed_greens_cf(ed_ctx* ctx, const ed_model* model, int prec, int n_states,
                  const ed_state* states, double beta, int n_w, int orbital, int spin,
                  int depth, double boltz_cut, double* G, double* coeffs, void* stream);
 
+/* ------------------------------------------------------- batched sectors */
+typedef struct ed_batch ed_batch;
+
+typedef struct ed_batch_info {
+  int steps;           /* Lanczos steps taken (the last sector to converge) */
+  int graph_replays;   /* replays of the one-step CUDA graph */
+  int n_sectors;
+  double total_ms;     /* wall time of the call */
+} ed_batch_info;
+
+/* Build n_sectors sectors (n_up[i], n_dn[i]) of one model for batched solves:
+ * all of a model's sectors (the Lehmann sum of Eq. 3 runs over every sector) or
+ * many small problems at once.  Tables live on the device; vectors are
+ * allocated per ed_batch_lanczos call.  Errors as ed_sector_create. */
+int ed_batch_create(ed_ctx* ctx, const ed_model* model, int n_sectors, const int* n_up, const int* n_dn,
+                    int prec, ed_batch** out);
+int ed_batch_destroy(ed_batch* b);
+/* Lowest k (<= 16) eigenvalues of every sector of the batch by Lanczos with full
+ * CGS2 reorthogonalisation (opts->reorth must be 1; v0 is ignored; seed seeds
+ * every sector's start vector).  All active sectors advance together: each
+ * step is one replay of a CUDA graph whose kernels (one H*v over all sectors,
+ * dot products, update, CGS2, norm, scaling) each run as a single launch over a
+ * device work list of (sector, 1024-element chunk) items; converged sectors
+ * drop out of the list.  evals: host, n_sectors * k (NaN past a sector's
+ * dimension); iters: host, n_sectors (may be NULL).  Synchronises. */
+int ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, double* evals, int* iters,
+                     ed_batch_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

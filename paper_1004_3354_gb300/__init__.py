@@ -60,6 +60,10 @@ class ed_lanczos_info(C.Structure):
                 ("apply_ms", C.c_double), ("total_ms", C.c_double)]
 
 
+class ed_batch_info(C.Structure):
+    _fields_ = [("steps", C.c_int), ("graph_replays", C.c_int), ("n_sectors", C.c_int), ("total_ms", C.c_double)]
+
+
 class ed_state(C.Structure):
     _fields_ = [("n_up", C.c_int), ("n_dn", C.c_int), ("E", C.c_double), ("vec", C.c_void_p)]
 
@@ -90,6 +94,11 @@ _SIGS = {
     "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
                                C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
+    "ed_batch_create": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.POINTER(C.c_void_p)]),
+    "ed_batch_destroy": (C.c_int, [C.c_void_p]),
+    "ed_batch_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
+                                   C.POINTER(ed_batch_info), C.c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -284,3 +293,33 @@ def torch_dtype(prec):
 def elems_per_value(prec) -> int:
     """torch elements per vector element (DF64 stores {hi, lo} float pairs)."""
     return 2 if PREC_NAMES.get(prec, prec) == ED_PREC_DF64 else 1
+
+
+# ------------------------------------------------------------ batched sectors
+def ed_batch_create(ctx, model, sectors, prec=ED_PREC_FP64):
+    """sectors: list of (n_up, n_dn)."""
+    mm = model if isinstance(model, Model) else Model(model)
+    nu = np.array([a for a, _ in sectors], dtype=np.int32)
+    nd = np.array([b for _, b in sectors], dtype=np.int32)
+    h = C.c_void_p()
+    check(lib().ed_batch_create(ctx, C.byref(mm.c), len(sectors), nu.ctypes.data_as(C.c_void_p),
+                                nd.ctypes.data_as(C.c_void_p), PREC_NAMES.get(prec, prec), C.byref(h)))
+    h._n = len(sectors)
+    return h
+
+
+def ed_batch_destroy(b):
+    return check(lib().ed_batch_destroy(b))
+
+
+def ed_batch_lanczos(b, n_sectors, k=8, tol=1e-10, max_iter=300, check_every=10, seed=1, stream=None,
+                     allow_not_converged=False):
+    """Returns (evals ndarray[n_sectors, k], iters ndarray[n_sectors], info, status)."""
+    o = ed_lanczos_opts(int(k), float(tol), int(max_iter), int(check_every), int(seed), None, 1)
+    ev = np.zeros(n_sectors * k, dtype=np.float64)
+    it = np.zeros(n_sectors, dtype=np.int32)
+    info = ed_batch_info()
+    st = lib().ed_batch_lanczos(b, C.byref(o), ev.ctypes.data_as(C.c_void_p), it.ctypes.data_as(C.c_void_p),
+                                C.byref(info), _stream(stream))
+    check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return ev.reshape(n_sectors, k), it, info, st

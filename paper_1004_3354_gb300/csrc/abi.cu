@@ -21,6 +21,8 @@ namespace {
 thread_local std::string g_err;
 }
 
+Ctx* ctx_of(ed_ctx* h) { return h ? &h->c : nullptr; }
+
 void set_error(const char* fmt, ...) {
   char buf[1024];
   va_list ap;

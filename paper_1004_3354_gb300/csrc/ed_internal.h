@@ -65,6 +65,9 @@ int dev_alloc_n(Ctx* c, T** p, size_t n) {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// The context behind an opaque handle (abi.cu).
+Ctx* ctx_of(ed_ctx* h);
+
 // --------------------------------------------------------- sector on device
 // Per-spin tables (device pointers).  Strings are uint32 bit masks.
 struct SpinTables {
