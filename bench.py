@@ -48,6 +48,8 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12"],
+                   help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12")
     return p.parse_args()
 
 
@@ -350,9 +352,61 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_sectors12(a):
+    """All 169 (N_up, N_dn) sectors of the N_s=12 three-orbital Kanamori model,
+    8 lowest states each: one batched solve (one CUDA-graph replay per Lanczos
+    step over every sector) against the same sectors solved one at a time."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    import workloads as W
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    model = W.kanamori(12, seed=0)
+    secs = [(u, d) for u in range(13) for d in range(13)]
+    ctx = ed.ed_ctx_create(0)
+    out = {"metric": "solves/s (all 169 sectors of N_s=12, 8 lowest each)", "unit": "sector solves/s",
+           "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded random bath)",
+           "config": {"workload": "three-orbital Kanamori N_s=12, all 169 sectors, k=8, tol 1e-10, full CGS2"},
+           "results": {}}
+    for prec in ("fp64", "fp32", "df64"):
+        b = ed.ed_batch_create(ctx, model, secs, prec)
+        tol = 1e-10 if prec != "fp32" else 1e-6
+        ed.ed_batch_lanczos(b, len(secs), k=8, tol=tol, max_iter=300, allow_not_converged=True)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, it, info, st = ed.ed_batch_lanczos(b, len(secs), k=8, tol=tol, max_iter=300,
+                                               allow_not_converged=True)
+        el = time.perf_counter() - t0
+        ed.ed_batch_destroy(b)
+        out["results"][f"batched_{prec}"] = {"seconds": el, "solves_per_s": len(secs) / el, "steps": info.steps,
+                                             "graph_replays": info.graph_replays,
+                                             "ground_energy_66": float(ev[6 * 13 + 6, 0])}
+    # one sector at a time, FP64, no batching or graphs
+    t0 = time.perf_counter()
+    e66 = None
+    for (u, d) in secs:
+        s = ed.ed_sector_create(ctx, model, u, d, "fp64")
+        ev, info, st = ed.ed_lanczos(s, k=8, tol=1e-10, max_iter=300, allow_not_converged=True)
+        if (u, d) == (6, 6):
+            e66 = float(ev[0])
+        ed.ed_sector_destroy(s)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["results"]["one_at_a_time_fp64"] = {"seconds": el, "solves_per_s": len(secs) / el, "ground_energy_66": e66}
+    out["value"] = out["results"]["batched_fp64"]["solves_per_s"]
+    out["speedup_batched_fp64_vs_one_at_a_time"] = out["results"]["batched_fp64"]["solves_per_s"] / \
+        out["results"]["one_at_a_time_fp64"]["solves_per_s"]
+    ed.ed_ctx_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "sectors12":
+        run_sectors12(a)
     else:
         run_ours(a)
