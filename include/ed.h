@@ -265,6 +265,67 @@ int ed_batch_destroy(ed_batch* b);
 int ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, double* evals, int* iters,
                      ed_batch_info* info, void* stream);
 
+/* ---------------------------------------------------------------- serving */
+/* A request server for impurity solves, the work of one DMFT iteration (Sec. 2:
+ * each iteration diagonalises a new impurity Hamiltonian and forms G(i w_n) of
+ * Eq. 3).  A server thread admits queued requests while their estimated device
+ * footprint fits the budget and a slot is free, and advances every admitted
+ * request a few Lanczos steps per pass on its own stream (continuous batching:
+ * requests join and leave between steps, their kernels overlap on the GPU).
+ * Per request: ground state of the sector by three-vector Lanczos, its Ritz
+ * vector, then (want_G) the particle and hole continued fractions of
+ * c+_{orbital,spin} at depth cf_depth and G on n_w Matsubara points at beta.
+ * A request's kernels touch only its own buffers, so its result is bitwise the
+ * same alone or in a mix.  The server's context must not be used from other
+ * threads while the server runs. */
+typedef struct ed_server ed_server;
+
+typedef struct ed_server_opts {
+  size_t hbm_budget;   /* device bytes the admitted requests may hold together (0 = no limit) */
+  int max_active;      /* requests on the GPU at once */
+  int prec;            /* vector format of every request */
+  double tol;          /* ground-state residual tolerance (relative, as ed_lanczos) */
+  int max_iter;        /* ground-state Lanczos steps at most */
+  int cf_depth;        /* continued-fraction depth (1..1000) */
+  int n_w;             /* Matsubara frequencies */
+  double beta;         /* inverse temperature */
+  uint64_t seed;       /* start-vector seed */
+} ed_server_opts;
+
+typedef struct ed_request {
+  const ed_model* model;  /* copied at submission */
+  int n_up, n_dn;         /* sector of the ground state */
+  int want_G;             /* also compute G(i w_n) */
+  int orbital, spin;      /* operator c+ of the Green's function */
+} ed_request;
+
+typedef struct ed_result {
+  int status;          /* ED_OK, ED_ERR_NOT_CONVERGED or the failure */
+  double E0;           /* ground energy of the sector */
+  int iters;           /* ground-state Lanczos steps */
+  double latency_ms;   /* submission to completion */
+  double queue_ms;     /* submission to admission */
+  int n_w;             /* G entries written (0 without want_G) */
+} ed_result;
+
+typedef struct ed_server_stats {
+  int queued, active, done, failed, max_active_seen;
+  size_t bytes_in_flight;   /* estimated footprint of the admitted requests */
+} ed_server_stats;
+
+/* Start a server on the context's device.  ED_ERR_INVALID on bad options. */
+int ed_server_create(ed_ctx* ctx, const ed_server_opts* opts, ed_server** out);
+/* Stop the thread and free everything (unpolled results are dropped). */
+int ed_server_destroy(ed_server* s);
+/* Queue a request; never blocks on the GPU.  ED_ERR_OOM if the request alone
+ * exceeds the whole budget, ED_ERR_INVALID for a bad model or sector. */
+int ed_submit(ed_server* s, const ed_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 and the result (and G, 2*n_w doubles re/im, if
+ * non-NULL) once the request has finished; the ticket is then released.
+ * ED_ERR_INVALID for an unknown or already collected ticket. */
+int ed_poll(ed_server* s, uint64_t ticket, ed_result* res, double* G, int* done);
+int ed_server_get_stats(ed_server* s, ed_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,27 @@ class ed_batch_info(C.Structure):
     _fields_ = [("steps", C.c_int), ("graph_replays", C.c_int), ("n_sectors", C.c_int), ("total_ms", C.c_double)]
 
 
+class ed_server_opts(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("prec", C.c_int), ("tol", C.c_double),
+                ("max_iter", C.c_int), ("cf_depth", C.c_int), ("n_w", C.c_int), ("beta", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class ed_request(C.Structure):
+    _fields_ = [("model", C.POINTER(ed_model)), ("n_up", C.c_int), ("n_dn", C.c_int), ("want_G", C.c_int),
+                ("orbital", C.c_int), ("spin", C.c_int)]
+
+
+class ed_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("E0", C.c_double), ("iters", C.c_int), ("latency_ms", C.c_double),
+                ("queue_ms", C.c_double), ("n_w", C.c_int)]
+
+
+class ed_server_stats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("done", C.c_int), ("failed", C.c_int),
+                ("max_active_seen", C.c_int), ("bytes_in_flight", C.c_size_t)]
+
+
 class ed_state(C.Structure):
     _fields_ = [("n_up", C.c_int), ("n_dn", C.c_int), ("E", C.c_double), ("vec", C.c_void_p)]
 
@@ -99,6 +120,11 @@ _SIGS = {
     "ed_batch_destroy": (C.c_int, [C.c_void_p]),
     "ed_batch_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                                    C.POINTER(ed_batch_info), C.c_void_p]),
+    "ed_server_create": (C.c_int, [C.c_void_p, C.POINTER(ed_server_opts), C.POINTER(C.c_void_p)]),
+    "ed_server_destroy": (C.c_int, [C.c_void_p]),
+    "ed_submit": (C.c_int, [C.c_void_p, C.POINTER(ed_request), C.POINTER(C.c_uint64)]),
+    "ed_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ed_result), C.c_void_p, C.POINTER(C.c_int)]),
+    "ed_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ed_server_stats)]),
 }
 
 EXPORTED = tuple(_SIGS)
@@ -323,3 +349,45 @@ def ed_batch_lanczos(b, n_sectors, k=8, tol=1e-10, max_iter=300, check_every=10,
                                 C.byref(info), _stream(stream))
     check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return ev.reshape(n_sectors, k), it, info, st
+
+
+# ---------------------------------------------------------------- serving
+def ed_server_create(ctx, hbm_budget=0, max_active=8, prec=ED_PREC_FP64, tol=1e-10, max_iter=400, cf_depth=100,
+                     n_w=1024, beta=40.0, seed=1):
+    o = ed_server_opts(int(hbm_budget), int(max_active), PREC_NAMES.get(prec, prec), float(tol), int(max_iter),
+                       int(cf_depth), int(n_w), float(beta), int(seed))
+    h = C.c_void_p()
+    check(lib().ed_server_create(ctx, C.byref(o), C.byref(h)))
+    h._n_w = int(n_w)
+    return h
+
+
+def ed_server_destroy(srv):
+    return check(lib().ed_server_destroy(srv))
+
+
+def ed_submit(srv, model, n_up, n_dn, want_G=True, orbital=None, spin=ED_SPIN_UP) -> int:
+    mm = model if isinstance(model, Model) else Model(model)
+    orb = int(getattr(mm.src, "orb0", 0)) if orbital is None else int(orbital)
+    r = ed_request(C.pointer(mm.c), int(n_up), int(n_dn), 1 if want_G else 0, orb, int(spin))
+    t = C.c_uint64()
+    check(lib().ed_submit(srv, C.byref(r), C.byref(t)))
+    return t.value
+
+
+def ed_poll(srv, ticket, n_w=None):
+    """Returns (done, ed_result or None, G complex ndarray or None)."""
+    nw = srv._n_w if n_w is None else n_w
+    res = ed_result()
+    G = np.zeros(2 * nw, dtype=np.float64)
+    done = C.c_int()
+    check(lib().ed_poll(srv, int(ticket), C.byref(res), G.ctypes.data_as(C.c_void_p), C.byref(done)))
+    if not done.value:
+        return False, None, None
+    return True, res, (G[0::2] + 1j * G[1::2]) if res.n_w else None
+
+
+def ed_server_get_stats(srv) -> ed_server_stats:
+    st = ed_server_stats()
+    check(lib().ed_server_get_stats(srv, C.byref(st)))
+    return st

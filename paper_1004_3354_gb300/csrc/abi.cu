@@ -36,7 +36,7 @@ int dev_alloc(Ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 1;
   if (c->budget && c->in_use + bytes > c->budget) {
-    set_error("HBM budget exceeded: %zu in use + %zu requested > %zu", c->in_use, bytes, c->budget);
+    set_error("HBM budget exceeded: %zu in use + %zu requested > %zu", c->in_use.load(), bytes, c->budget);
     return ED_ERR_OOM;
   }
   cudaError_t e = cudaMalloc(p, bytes);
@@ -57,7 +57,9 @@ void dev_free(Ctx* c, void* p, size_t bytes) {
   if (!p) return;
   cudaFree(p);
   if (bytes == 0) bytes = 1;
-  c->in_use -= std::min(c->in_use, bytes);
+  size_t cur = c->in_use.load();
+  while (!c->in_use.compare_exchange_weak(cur, cur - std::min(cur, bytes))) {
+  }
 }
 
 int convert_async(const void* src, int sp, void* dst, int dp, uint64_t n, cudaStream_t st);
@@ -198,7 +200,7 @@ int ed_ctx_destroy(ed_ctx* ctx) {
 
 int ed_ctx_bytes_in_use(const ed_ctx* ctx, size_t* out) {
   if (!ctx || !out) ED_INVALID("NULL argument");
-  *out = ctx->c.in_use;
+  *out = ctx->c.in_use.load();
   return ED_OK;
 }
 

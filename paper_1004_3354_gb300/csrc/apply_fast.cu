@@ -593,7 +593,7 @@ int build_fast(Sector* s) {
     k_df_copy<<<(unsigned)(((uint64_t)f.n_pat * NE + 255) / 256), 256>>>(f.dd, f.dd_df, (uint64_t)f.n_pat * NE);
     ED_LAUNCH_CHECK();
   }
-  ED_TRY_CUDA(cudaDeviceSynchronize());
+  ED_TRY_CUDA(cudaStreamSynchronize(0));  // legacy stream only: leaves other work running
   f.ok = true;
   return ED_OK;
 }

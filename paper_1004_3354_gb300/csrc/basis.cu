@@ -487,7 +487,7 @@ int build_sector(Ctx* ctx, const ed_model* m, int n_up, int n_dn, int prec, Sect
       ED_LAUNCH_CHECK();
     }
   }
-  ED_TRY_CUDA(cudaDeviceSynchronize());
+  ED_TRY_CUDA(cudaStreamSynchronize(0));  // legacy stream only: leaves other work running
   return ED_OK;
 }
 

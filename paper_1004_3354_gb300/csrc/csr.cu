@@ -171,7 +171,7 @@ int build_csr(Sector* s) {
   ED_TRY(sector_alloc(s, &s->csr_val, s->csr_nnz));
   k_csr_fill<<<grid, 128>>>(S, s->up.basis, s->dn.basis, s->csr_ptr, s->csr_col, s->csr_val);
   ED_LAUNCH_CHECK();
-  ED_TRY_CUDA(cudaDeviceSynchronize());
+  ED_TRY_CUDA(cudaStreamSynchronize(0));  // legacy stream only: leaves other work running
   return ED_OK;
 }
 

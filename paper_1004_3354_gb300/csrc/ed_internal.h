@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -45,7 +46,7 @@ void set_error(const char* fmt, ...);
 struct Ctx {
   int device = 0;
   size_t budget = 0;      // 0 = unlimited
-  size_t in_use = 0;
+  std::atomic<size_t> in_use{0};
   int num_sms = 0;
   size_t smem_optin = 0;
   uint32_t* d_binom = nullptr;   // [33][33] binomial coefficients C(n, k)

@@ -83,6 +83,14 @@ struct SectorCache {
 
 }  // namespace
 
+// Add one (state, part) continued fraction to G on `st` (used by the server).
+int greens_accumulate(double2* dG, int n_w, double beta, const double* da, const double* db, int L, double n2,
+                      const double* dE, int n_states, int nu, int sgn, cudaStream_t st) {
+  k_cf_accum<<<(n_w + 127) / 128, 128, 0, st>>>(dG, n_w, beta, da, db, L, n2, dE, n_states, nu, sgn);
+  ED_LAUNCH_CHECK();
+  return ED_OK;
+}
+
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
                   int n_w, int orbital, int spin, int depth, double boltz_cut, double* G, double* coeffs,
                   cudaStream_t st) {

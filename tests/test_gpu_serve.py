@@ -1,0 +1,111 @@
+"""The request server: results against the oracle, the same result alone and
+in a mix (continuous batching), HBM-footprint admission, poll semantics."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sector as osec, spectrum, greens as og
+from tests._gpu import ensure_built, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = torch_cuda()
+    ed = ensure_built()
+    ctx = ed.ed_ctx_create(0)
+    yield ed, ctx, torch
+    ed.ed_ctx_destroy(ctx)
+
+
+def wait_all(ed, srv, tickets, timeout=300.0):
+    out, t0 = {}, time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            done, res, G = ed.ed_poll(srv, t)
+            if done:
+                out[t] = (res.status, res.E0, res.iters, G, res.latency_ms)
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        time.sleep(0.002)
+    return out
+
+
+def request_set():
+    reqs = []
+    for i, ns in enumerate((8, 9, 10, 11, 12, 10, 9)):
+        reqs.append((W.kanamori(ns, seed=100 + i), (ns + 1) // 2, ns // 2))
+    return reqs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_server_results_match_oracle_and_are_mix_invariant(env, prec):
+    ed, ctx, torch = env
+    beta, nw, depth = 40.0, 256, 60
+    reqs = request_set()
+    srv = ed.ed_server_create(ctx, max_active=4, prec=prec, tol=1e-11, max_iter=400, cf_depth=depth, n_w=nw,
+                              beta=beta)
+    try:
+        # request 0 alone
+        t_alone = ed.ed_submit(srv, reqs[0][0], reqs[0][1], reqs[0][2])
+        alone = wait_all(ed, srv, [t_alone])[t_alone]
+        # the same request again, now arriving in the middle of a mix
+        ts = [ed.ed_submit(srv, m, nu, nd) for (m, nu, nd) in reqs[1:4]]
+        t_mix = ed.ed_submit(srv, reqs[0][0], reqs[0][1], reqs[0][2])
+        ts += [ed.ed_submit(srv, m, nu, nd) for (m, nu, nd) in reqs[4:]]
+        res = wait_all(ed, srv, ts + [t_mix])
+        mix = res[t_mix]
+        assert alone[0] == 0 and mix[0] == 0
+        assert alone[1] == mix[1]                      # bit for bit
+        assert np.array_equal(alone[3], mix[3])
+        # every request against the oracle: ground energy and G
+        for (m, nu, nd), t in zip(reqs[1:4] + reqs[4:], ts):
+            st, E0, iters, G, lat = res[t]
+            assert st == 0
+            H = osec.build_csr(m, nu, nd)
+            w, v = spectrum.lowest(H, 1, vectors=True)
+            assert abs(E0 - w[0]) <= 1e-10 * abs(w[0]), (m.n_s, E0, w[0])
+            Gref = og.greens_cf(m, [(nu, nd, w[0], v[:, 0])], beta, nw, m.orb0, 0, depth=depth)
+            assert np.max(np.abs(G - Gref)) <= 1e-8, (m.n_s, np.max(np.abs(G - Gref)))
+        stats = ed.ed_server_get_stats(srv)
+        assert stats.max_active_seen >= 2          # requests overlapped on the device
+        assert stats.failed == 0
+    finally:
+        ed.ed_server_destroy(srv)
+
+
+def test_server_admission_budget_and_errors(env):
+    ed, ctx, torch = env
+    reqs = request_set()
+    budget = 96 * 1024 * 1024 + 200 * 1024 * 1024   # about two of these requests at once
+    srv = ed.ed_server_create(ctx, hbm_budget=budget, max_active=16, prec="fp64", tol=1e-10, cf_depth=30, n_w=32)
+    try:
+        ts = [ed.ed_submit(srv, m, nu, nd) for (m, nu, nd) in reqs]
+        seen = 0
+        t0 = time.time()
+        while True:
+            st = ed.ed_server_get_stats(srv)
+            assert st.bytes_in_flight <= budget
+            seen = max(seen, st.active)
+            if st.done + st.failed == len(ts):
+                break
+            assert time.time() - t0 < 300
+            time.sleep(0.001)
+        res = wait_all(ed, srv, ts)
+        assert all(r[0] == 0 for r in res.values())
+        # a request larger than the whole budget is refused at submission
+        big = W.kanamori(16, seed=1)
+        with pytest.raises(ed.EdError) as e:
+            ed.ed_submit(srv, big, 8, 8)
+        assert e.value.status == ed.ED_ERR_OOM
+        # collected and unknown tickets
+        with pytest.raises(ed.EdError):
+            ed.ed_poll(srv, ts[0])
+        with pytest.raises(ed.EdError):
+            ed.ed_poll(srv, 10 ** 9)
+    finally:
+        ed.ed_server_destroy(srv)
