@@ -48,8 +48,10 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12"],
-                   help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12")
+    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve"],
+                   help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12; "
+                        "serve: Poisson stream of impurity solves, N_s in 10..16")
+    p.add_argument("--requests", type=int, default=40)
     return p.parse_args()
 
 
@@ -402,11 +404,92 @@ def run_sectors12(a):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(a):
+    """Impurity-solve requests (three-orbital Kanamori, N_s uniform in 10..16,
+    ground sector around half filling, G(i w_n) of orbital 0 spin up on 1024
+    Matsubara points at beta = 40, CF depth 100) served with continuous
+    batching, against the plain FP64 path solving them one at a time."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    import workloads as W
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    beta, nw, depth, tol = 40.0, 1024, 100, 1e-10
+    stream = W.serving_stream(a.requests, seed=0, rate=1.0, ns_range=(10, 16))
+    models = [W.kanamori(r["n_s"], seed=r["model_seed"]) for r in stream]
+    ctx = ed.ed_ctx_create(0)
+    # plain FP64, one at a time (no batching, no graphs, FP64 vectors)
+    base_E, base_lat = [], []
+    t_all = time.perf_counter()
+    for r, m in zip(stream, models):
+        t0 = time.perf_counter()
+        sec = ed.ed_sector_create(ctx, m, r["n_up"], r["n_dn"], "fp64", ed.ED_SECTOR_GENERIC)
+        dim = ed.ed_sector_get_info(sec).dim
+        psi = torch.empty(dim, dtype=torch.float64, device="cuda")
+        ev, info, st = ed.ed_lanczos(sec, k=1, tol=tol, max_iter=400, reorth=False, evecs=psi,
+                                     allow_not_converged=True)
+        ed.ed_greens_cf(ctx, m, "fp64", [(r["n_up"], r["n_dn"], float(ev[0]), psi)], beta, nw, orbital=m.orb0,
+                        spin=0, depth=depth)
+        ed.ed_sector_destroy(sec)
+        del psi
+        base_E.append(float(ev[0]))
+        base_lat.append(1e3 * (time.perf_counter() - t0))
+    base_total = time.perf_counter() - t_all
+    base_rate = len(stream) / base_total
+    out = {"metric": "impurity solves/s served (N_s 10..16, ground state + G(i w_n))", "unit": "solves/s",
+           "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded random baths, Poisson arrivals)",
+           "config": {"workload": f"{len(stream)} requests, three-orbital Kanamori N_s~U{{10..16}}, "
+                                  f"sector ((N+1)/2, N/2), tol {tol}, CF depth {depth}, n_w {nw}, beta {beta}"},
+           "plain_fp64_one_at_a_time": {"solves_per_s": base_rate, "seconds": base_total,
+                                        "p50_ms": float(np.percentile(base_lat, 50)),
+                                        "p99_ms": float(np.percentile(base_lat, 99))}}
+    budget = 200 * 1024 ** 3
+    for prec in ("fp32", "df64"):
+        for mode in ("saturation", "poisson"):
+            srv = ed.ed_server_create(ctx, hbm_budget=budget, max_active=16, prec=prec, tol=tol if prec != "fp32" else 1e-6,
+                                      max_iter=400, cf_depth=depth, n_w=nw, beta=beta)
+            rate = 0.8 * base_rate
+            arrivals = [0.0] * len(stream) if mode == "saturation" else [r["t_arrive"] / rate for r in stream]
+            tickets, results = [None] * len(stream), {}
+            t0 = time.perf_counter()
+            i = 0
+            while len(results) < len(stream):
+                now = time.perf_counter() - t0
+                while i < len(stream) and arrivals[i] <= now:
+                    tickets[i] = ed.ed_submit(srv, models[i], stream[i]["n_up"], stream[i]["n_dn"])
+                    i += 1
+                for q in range(i):
+                    if q in results:
+                        continue
+                    done, res, G = ed.ed_poll(srv, tickets[q])
+                    if done:
+                        results[q] = (res.status, res.E0, res.latency_ms)
+                time.sleep(0.0005)
+            el = time.perf_counter() - t0
+            stats = ed.ed_server_get_stats(srv)
+            ed.ed_server_destroy(srv)
+            lat = [results[q][2] for q in range(len(stream))]
+            relerr = max(abs(results[q][1] - base_E[q]) / abs(base_E[q]) for q in range(len(stream)))
+            out[f"served_{prec}_{mode}"] = {
+                "solves_per_s": len(stream) / el, "seconds": el, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_rel_E0_err_vs_fp64": relerr,
+                "failed": sum(1 for q in results if results[q][0] != 0), "max_active_seen": stats.max_active_seen,
+                "arrival_rate_per_s": None if mode == "saturation" else rate}
+    ed.ed_ctx_destroy(ctx)
+    out["value"] = out["served_fp32_saturation"]["solves_per_s"]
+    out["speedup_served_fp32_vs_plain_fp64"] = out["value"] / base_rate
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sectors12":
         run_sectors12(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)
