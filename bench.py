@@ -48,9 +48,10 @@ def args_parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve"],
+    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15"],
                    help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12; "
-                        "serve: Poisson stream of impurity solves, N_s in 10..16")
+                        "serve: Poisson stream of impurity solves, N_s in 10..16; "
+                        "solve15: N_s=15 ground state + G(i w_n) per vector format, and the stored-CSR H*v")
     p.add_argument("--requests", type=int, default=40)
     return p.parse_args()
 
@@ -483,6 +484,72 @@ def run_serve(a):
     print(json.dumps(out), flush=True)
 
 
+def run_solve15(a):
+    """The N_s=15 (7,8) sector: ground state (three-vector Lanczos) and the
+    continued-fraction G(i w_n) on 1024 Matsubara points at beta = 40, in FP64,
+    DF64 and FP32 vectors; the stored-CSR H*v (FP64) beside the matrix-free one."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    import workloads as W
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    m = W.kanamori(NS, seed=SEED)
+    dim = W.sector_dim(NS, NUP, NDN)
+    ctx = ed.ed_ctx_create(0)
+    out = {"metric": "N_s=15 ground state + G(i w_n): time and error per vector format", "n_gpus": 1,
+           "data": "synthetic (seeded random bath)", "config": workload_config("fp64", dim), "results": {}}
+    ref_E, ref_G = None, None
+    for prec in ("fp64", "df64", "fp32"):
+        p = ed.PREC_NAMES[prec]
+        sec = ed.ed_sector_create(ctx, m, NUP, NDN, prec)
+        psi = torch.empty(dim * ed.elems_per_value(p), dtype=ed.torch_dtype(p), device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-10 if prec != "fp32" else 1e-7, max_iter=500, reorth=False,
+                                     evecs=psi, allow_not_converged=True)
+        t1 = time.perf_counter()
+        G = ed.ed_greens_cf(ctx, m, prec, [(NUP, NDN, float(ev[0]), psi)], 40.0, 1024, orbital=m.orb0, spin=0,
+                            depth=150)
+        t2 = time.perf_counter()
+        ed.ed_sector_destroy(sec)
+        del psi
+        r = {"E0": float(ev[0]), "lanczos_steps": info.iters, "ground_state_s": t1 - t0,
+             "apply_ms_total": info.apply_ms, "greens_s": t2 - t1, "status": st}
+        if prec == "fp64":
+            ref_E, ref_G = float(ev[0]), G
+        else:
+            r["rel_E0_err_vs_fp64"] = abs(float(ev[0]) - ref_E) / abs(ref_E)
+            r["max_abs_G_err_vs_fp64"] = float(np.max(np.abs(G - ref_G)))
+        out["results"][prec] = r
+    # stored CSR vs matrix-free, FP64
+    sec = ed.ed_sector_create(ctx, m, NUP, NDN, "fp64", ed.ED_SECTOR_CSR)
+    info = ed.ed_sector_get_info(sec)
+    x = torch.from_numpy(W.random_vector(dim, seed=1)).cuda()
+    y1, y2 = torch.empty_like(x), torch.empty_like(x)
+    for f in (ed.ed_apply_h_csr, ed.ed_apply_h):
+        f(sec, x, y1)
+    torch.cuda.synchronize()
+    res = {}
+    for name, f, y in (("csr", ed.ed_apply_h_csr, y1), ("matrix_free", ed.ed_apply_h, y2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            f(sec, x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / 10
+    csr_bytes = info.csr_nnz * 12 + (dim + 1) * 8 + 2 * dim * 8
+    out["csr_vs_matrix_free_fp64"] = {
+        "csr_nnz": info.csr_nnz, "csr_ms": res["csr"], "matrix_free_ms": res["matrix_free"],
+        "csr_GB_per_s_of_its_bytes": csr_bytes / (res["csr"] * 1e-3) / 1e9,
+        "csr_bytes_per_apply": csr_bytes, "max_abs_diff": float((y1 - y2).abs().max())}
+    ed.ed_sector_destroy(sec)
+    ed.ed_ctx_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = args_parse()
     if a.impl == "reference":
@@ -491,5 +558,7 @@ if __name__ == "__main__":
         run_sectors12(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "solve15":
+        run_solve15(a)
     else:
         run_ours(a)
