@@ -147,10 +147,15 @@ def cpu_baseline(model, x, prec, seconds):
                       f"GB/s = rows/s x {2 * eb} B"}
 
 
+def row_kernel(prec):
+    """The fast row kernel that ed_apply_h launches for this vector format."""
+    return "k_apply_pair" if prec == "fp32" else "k_apply_win"
+
+
 def traffic_for(kernel_src_sha, prec):
     """DRAM bytes per launch of the row kernel from the committed ncu summary,
     only if it was captured from the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"k_apply_win_{prec}_n15_traffic.txt")
+    p = os.path.join(ROOT, "profiles", f"{row_kernel(prec)}_{prec}_n15_traffic.txt")
     try:
         kv = dict(line.split(":", 1) for line in open(p) if ":" in line)
     except Exception:
@@ -292,7 +297,8 @@ def run_ours(a):
             s1.record(stream)
             torch.cuda.synchronize()
             msq = s0.elapsed_time(s1) / n_q
-            extras[q] = {"ms_per_apply": msq, "GB/s": alg_bytes(q, dim) / (msq * 1e-3) / 1e9}
+            extras[q] = {"ms_per_apply": msq, "GB/s": alg_bytes(q, dim) / (msq * 1e-3) / 1e9,
+                         "kernel": row_kernel(q)}
             del xq, yq
             ed.ed_sector_destroy(s2)
 
@@ -309,7 +315,7 @@ def run_ours(a):
         "pct_hbm_peak": round(100 * value / world / peak, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic_for(sha, a.prec),
-                     "kernel": "k_apply_win", "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": row_kernel(a.prec), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
                      "apply_src_sha": sha},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,

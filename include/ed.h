@@ -109,7 +109,8 @@ typedef struct ed_sector_info {
   uint64_t csr_nnz;             /* stored CSR entries (0 without ED_SECTOR_CSR) */
   uint64_t table_bytes;         /* device bytes held by the sector */
   double   nnz_per_row;         /* mean stored entries per row of H (diagonal included) */
-  int      kernel;              /* H*v kernel: 0 flat, 1 row-staged generic, 2 fast row kernel */
+  int      kernel;              /* H*v kernel: 0 flat, 1 row-staged generic, 2 fast row kernel,
+                                   3 fast two-row kernel (FP32 vectors) */
 } ed_sector_info;
 
 /* ------------------------------------------------------------------ errors */

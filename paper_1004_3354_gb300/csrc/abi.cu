@@ -261,7 +261,7 @@ int ed_sector_get_info(const ed_sector* h, ed_sector_info* out) {
       mix = (double)s.n_mix / s.up.D * (num / den);
     }
   }
-  out->kernel = s.fast.ok ? 2 : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
+  out->kernel = s.fast.ok ? (s.fast.pair ? 3 : 2) : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
   out->nnz_per_row = 1.0 + (double)s.dn.n_hops / std::max<uint32_t>(s.dn.D, 1) +
                      (double)s.up.n_hops / std::max<uint32_t>(s.up.D, 1) + mix;
   return ED_OK;

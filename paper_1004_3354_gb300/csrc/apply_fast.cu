@@ -327,6 +327,309 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
   }
 }
 
+// ---------------------------------------------------------------- two rows
+// Float vectors run two rows per block: rows A and B share every down hop
+// (same hop word, same coefficient, same staged offset), so the two rows are
+// staged interleaved ({A, B} per rank), the coefficients are kept as
+// {hi, hi, lo, lo}, and one f32x2 instruction advances both rows' double-float
+// accumulators.  Hop words, window permutation and coefficient loads are
+// shared by the two rows.  (Double-float rows would need 16 bytes per rank:
+// two blocks of that size leave the SM too little L1, and the single-row
+// kernel is faster for them.)
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g));
+}
+
+template <class P>
+struct PairTraits;
+
+template <>
+struct PairTraits<PolF32> {
+  using PV = float2;  // {A, B}
+  static constexpr bool XLO = false;
+  __device__ static __forceinline__ float2 hi(const PV& v) { return v; }
+  __device__ static __forceinline__ float2 lo(const PV&) { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ float2 hi2(float a, float b) { return make_float2(a, b); }
+  __device__ static __forceinline__ float2 lo2(float, float) { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ void stage(PV* s, const float* a, const float* b) {
+    cp_async4(&s->x, a);
+    cp_async4(&s->y, b);
+  }
+  __device__ static __forceinline__ float out(float h, float l) { return __fadd_rn(h, l); }
+  __device__ static __forceinline__ float xa(const PV& v) { return v.x; }
+  __device__ static __forceinline__ float xb(const PV& v) { return v.y; }
+};
+
+template <class P>
+size_t pair_smem(uint32_t D, int n_coef) {
+  return align16(D * sizeof(typename PairTraits<P>::PV)) + align16((size_t)n_coef * 16) + 4 * align16(kList * 16) +
+         align16(kList * 8) + align16(kMaxDelta * 4);
+}
+
+// coefficient pair (sa * c_A, sb * c_B) from a {A.hi, B.hi, A.lo, B.lo} entry, sa, sb in {0, 1, -1}
+__device__ __forceinline__ float4 sign_pair(float4 c, int32_t mda, int32_t mdb) {
+  if (mda == INT_MIN) c.x = c.z = 0.f;
+  else if (mda & 1) c.x = -c.x, c.z = -c.z;
+  if (mdb == INT_MIN) c.y = c.w = 0.f;
+  else if (mdb & 1) c.y = -c.y, c.w = -c.w;
+  return c;
+}
+
+template <class P, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typename P::V* __restrict__ x,
+                                                        typename P::V* __restrict__ y) {
+  using V = typename P::V;
+  using A = typename P::A;
+  using T = PairTraits<P>;
+  using PV = typename T::PV;
+  constexpr bool XLO = T::XLO;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const uint32_t D = F.D;
+  unsigned char* p = sm;
+  PV* xs = reinterpret_cast<PV*>(p);            // interleaved rows A and B
+  p += align16(D * sizeof(PV));
+  float4* cs = reinterpret_cast<float4*>(p);    // {hi, hi, lo, lo} per distinct down-hop element
+  p += align16((size_t)F.n_coef * 16);
+  float4* lc = reinterpret_cast<float4*>(p);    // up-hop coefficients {A.hi, B.hi, A.lo, B.lo}
+  p += align16(kList * 16);
+  float4* mc = reinterpret_cast<float4*>(p);    // mixed coefficients, same layout
+  p += align16(kList * 16);
+  ulonglong2* lr = reinterpret_cast<ulonglong2*>(p);  // up-hop row offsets (elements) of A and B
+  p += align16(kList * 16);
+  ulonglong2* mr = reinterpret_cast<ulonglong2*>(p);  // mixed row offsets
+  p += align16(kList * 16);
+  uint2* mm = reinterpret_cast<uint2*>(p);            // mixed move offsets, ~0u for padding
+  p += align16(kList * 8);
+  int32_t* mds = reinterpret_cast<int32_t*>(p);       // move shifts per pattern
+  __shared__ int n_up_s, n_mx_s;
+  __shared__ uint32_t pat_s[2];
+  const bool mixd = F.dpat4 != nullptr;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NWARP = BS / 32;
+  const uint64_t NE = (uint64_t)F.n_win * kWin;
+  constexpr uint32_t kPad = 0xffffffffu;
+
+  for (int k = threadIdx.x; k < F.n_coef; k += BS) {
+    const float2 c = F.coef_df[k];
+    cs[k] = make_float4(c.x, c.x, c.y, c.y);
+  }
+  for (int k = threadIdx.x; k < F.n_md; k += BS) mds[k] = F.mdelta[k];
+  A dacc = P::zero();  // <x, y> over this thread's elements (only used with F.dotp)
+
+  const uint32_t n_pairs = (F.D_up + 1) / 2;
+  for (uint32_t i = blockIdx.x; i < n_pairs; i += gridDim.x) {
+    const uint32_t uA = F.row_order[2 * i];
+    const bool hasB = 2 * i + 1 < F.D_up;
+    const uint32_t uB = hasB ? F.row_order[2 * i + 1] : uA;
+    __syncthreads();
+    {
+      const V* xa = x + (uint64_t)uA * D;
+      const V* xb = x + (uint64_t)uB * D;
+      for (uint32_t d = threadIdx.x; d < D; d += BS) T::stage(xs + d, xa + d, xb + d);
+    }
+    // up-hop lists of A and B side by side; the shorter one is padded with a
+    // zero coefficient on its own row
+    const uint32_t a0 = F.uh_ptr[uA], na = F.uh_ptr[uA + 1] - a0;
+    const uint32_t b0 = F.uh_ptr[uB], nb = hasB ? F.uh_ptr[uB + 1] - b0 : 0u;
+    const uint32_t nh = na > nb ? na : nb;
+    for (uint32_t k = threadIdx.x; k < nh; k += BS) {
+      const float2 ca = k < na ? F.uh_val_df[a0 + k] : make_float2(0.f, 0.f);
+      const float2 cb = k < nb ? F.uh_val_df[b0 + k] : make_float2(0.f, 0.f);
+      lr[k] = make_ulonglong2((unsigned long long)(k < na ? F.uh_tgt[a0 + k] : uA) * D,
+                              (unsigned long long)(k < nb ? F.uh_tgt[b0 + k] : uB) * D);
+      lc[k] = make_float4(ca.x, cb.x, ca.y, cb.y);
+    }
+    uint32_t nm = 0;
+    if (F.mx_ptr) {
+      const uint32_t ma0 = F.mx_ptr[uA], ma = F.mx_ptr[uA + 1] - ma0;
+      const uint32_t mb0 = F.mx_ptr[uB], mb = hasB ? F.mx_ptr[uB + 1] - mb0 : 0u;
+      nm = ma > mb ? ma : mb;
+      const uint32_t stride = mixd ? (uint32_t)F.np : D;
+      for (uint32_t k = threadIdx.x; k < nm; k += BS) {
+        const float2 ca = k < ma ? F.mx_val_df[ma0 + k] : make_float2(0.f, 0.f);
+        const float2 cb = k < mb ? F.mx_val_df[mb0 + k] : make_float2(0.f, 0.f);
+        mr[k] = make_ulonglong2((unsigned long long)(k < ma ? F.mx_tgt[ma0 + k] : uA) * D,
+                                (unsigned long long)(k < mb ? F.mx_tgt[mb0 + k] : uB) * D);
+        mc[k] = make_float4(ca.x, cb.x, ca.y, cb.y);
+        mm[k] = make_uint2(k < ma ? (uint32_t)F.mx_mv[ma0 + k] * stride : kPad,
+                           k < mb ? (uint32_t)F.mx_mv[mb0 + k] * stride : kPad);
+      }
+    }
+    if (threadIdx.x == 0) {
+      n_up_s = (int)nh;
+      n_mx_s = (int)nm;
+      pat_s[0] = F.row_pat[uA];
+      pat_s[1] = F.row_pat[uB];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const float2 euA = F.e_up_df[uA], euB = F.e_up_df[uB];
+    const float2 EUh = make_float2(euA.x, euB.x), EUl = make_float2(euA.y, euB.y);
+    const int nup = n_up_s, nmx = n_mx_s;
+    const float2* ddA = F.dd_df + (uint64_t)pat_s[0] * NE;
+    const float2* ddB = F.dd_df + (uint64_t)pat_s[1] * NE;
+    V* yA = y + (uint64_t)uA * D;
+    V* yB = y + (uint64_t)uB * D;
+    for (uint32_t w = warp; w < F.n_win; w += NWARP) {
+      const uint32_t ent = w * 32 + lane;  // this lane's four entries
+      const uint4 dq = __ldg(F.perm4 + ent);
+      uint32_t dv[4];
+      bool ok[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t d = sel4(dq, e);
+        ok[e] = d < D;
+        dv[e] = ok[e] ? d : 0u;
+      }
+      float2 dga[4], dgb[4];
+      ld4<float2>(ddA + 4 * (uint64_t)ent, dga);
+      ld4<float2>(ddB + 4 * (uint64_t)ent, dgb);
+      float2 H[4], L[4];  // (A, B) hi and lo parts of the four slots
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const PV X = xs[dv[e]];
+        H[e] = L[e] = make_float2(0.f, 0.f);
+        df_mac2<XLO>(H[e], L[e], make_float2(dga[e].x, dgb[e].x), make_float2(dga[e].y, dgb[e].y), T::hi(X),
+                     T::lo(X));
+        df_mac2<XLO>(H[e], L[e], EUh, EUl, T::hi(X), T::lo(X));
+      }
+      // down hops: slot counts descend (c0 >= c1 >= c2 >= c3)
+      {
+        const uchar4 c4 = __ldg(F.cnt4 + w);
+        const uint4* hp = F.hop4 + (uint64_t)w * F.max_cnt * 32 + lane;
+        const int c0 = c4.x, c1 = c4.y, c2 = c4.z, c3 = c4.w;
+        int k = 0;
+#define ED_HOP(E, WD)                                                                                      \
+  do {                                                                                                     \
+    const float4 cc = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(cs) + ((WD) & 0x1fffu)); \
+    const PV X = *reinterpret_cast<const PV*>(reinterpret_cast<const unsigned char*>(xs) + ((WD) >> 13));  \
+    df_mac2<XLO>(H[E], L[E], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi(X), T::lo(X));        \
+  } while (0)
+        for (; k < c3; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y); ED_HOP(2, h.z); ED_HOP(3, h.w);
+        }
+        for (; k < c2; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y); ED_HOP(2, h.z);
+        }
+        for (; k < c1; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x); ED_HOP(1, h.y);
+        }
+        for (; k < c0; ++k) {
+          const uint4 h = __ldg(hp + (uint64_t)k * 32);
+          ED_HOP(0, h.x);
+        }
+#undef ED_HOP
+      }
+      // up hops: the k-th neighbour row of A and of B
+      for (int k = 0; k < nup; ++k) {
+        const ulonglong2 R = lr[k];
+        const float4 cc = lc[k];
+        V a[4], b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          a[e] = __ldg(x + R.x + dv[e]);
+          b[e] = __ldg(x + R.y + dv[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
+                       T::lo2(a[e], b[e]));
+      }
+      // spin-flip / pair-hop
+      if (nmx) {
+        const uint32_t wp = mixd ? F.wpat[w] : 0xffffffffu;
+        if (wp != 0xffffffffu) {
+          // every string of the window has impurity pattern wp: one shift per row
+          for (int j = 0; j < nmx; ++j) {
+            const uint2 M = mm[j];
+            const int32_t mda = M.x != kPad ? mds[M.x + wp] : INT_MIN;
+            const int32_t mdb = M.y != kPad ? mds[M.y + wp] : INT_MIN;
+            if (mda == INT_MIN && mdb == INT_MIN) continue;
+            const ulonglong2 R = mr[j];
+            const float4 cc = sign_pair(mc[j], mda, mdb);
+            const V* xa = x + R.x + (mda == INT_MIN ? 0 : (mda >> 1));
+            const V* xb = x + R.y + (mdb == INT_MIN ? 0 : (mdb >> 1));
+            V a[4], b[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              a[e] = ok[e] ? __ldg(xa + dv[e]) : x[0];
+              b[e] = ok[e] ? __ldg(xb + dv[e]) : x[0];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
+                           T::lo2(a[e], b[e]));
+          }
+        } else {
+          // per-lane shifts: from the entry's impurity pattern, or the generic move tables
+          const uint32_t pd4 = mixd ? __ldg(F.dpat4 + ent) : 0u;
+          for (int j = 0; j < nmx; ++j) {
+            const uint2 M = mm[j];
+            const ulonglong2 R = mr[j];
+            const float4 c0 = mc[j];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              int32_t mda = INT_MIN, mdb = INT_MIN;
+              uint64_t ia = 0, ib = 0;
+              if (ok[e]) {
+                if (mixd) {
+                  const uint32_t pe = (pd4 >> (8 * e)) & 255u;
+                  if (M.x != kPad) mda = mds[M.x + pe];
+                  if (M.y != kPad) mdb = mds[M.y + pe];
+                  if (mda != INT_MIN) ia = R.x + (uint64_t)((int64_t)dv[e] + (mda >> 1));
+                  if (mdb != INT_MIN) ib = R.y + (uint64_t)((int64_t)dv[e] + (mdb >> 1));
+                } else {
+                  if (M.x != kPad) {
+                    const int32_t v = __ldg(F.mv + M.x + dv[e]);
+                    if (v >= 0) mda = v, ia = R.x + (uint32_t)(v >> 1);
+                  }
+                  if (M.y != kPad) {
+                    const int32_t v = __ldg(F.mv + M.y + dv[e]);
+                    if (v >= 0) mdb = v, ib = R.y + (uint32_t)(v >> 1);
+                  }
+                }
+              }
+              if (mda == INT_MIN && mdb == INT_MIN) continue;
+              const float4 cc = sign_pair(c0, mda, mdb);
+              const V a = __ldg(x + ia), b = __ldg(x + ib);
+              df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a, b),
+                           T::lo2(a, b));
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (ok[e]) {
+          const V ya = T::out(H[e].x, L[e].x);
+          st_stream(yA + dv[e], ya);
+          if (F.dotp) P::dot(dacc, T::xa(xs[dv[e]]), ya);
+          if (hasB) {
+            const V yb = T::out(H[e].y, L[e].y);
+            st_stream(yB + dv[e], yb);
+            if (F.dotp) P::dot(dacc, T::xb(xs[dv[e]]), yb);
+          }
+        }
+    }
+  }
+  if (F.dotp) {
+    __shared__ A red[BS / 32];
+    dacc = P::warp_sum(dacc);
+    if (lane == 0) red[warp] = dacc;
+    __syncthreads();
+    if (warp == 0) {
+      A v = lane < NWARP ? red[lane] : P::zero();
+      v = P::warp_sum(v);
+      if (lane == 0) F.dotp[blockIdx.x] = P::to_double(v);
+    }
+  }
+}
+
 // Window tables: entry idx = w*128 + lane*4 + slot holds down rank perm[idx]
 // (D for padding).  Hop words of entry idx at [w][k][lane][slot].
 __global__ void k_win_tables(uint32_t D, uint32_t n_win, uint32_t max_cnt, const uint32_t* __restrict__ perm,
@@ -453,12 +756,34 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double
   return ED_OK;
 }
 
-// Three 256-thread blocks per SM for 8-byte elements (shared memory and
-// registers both bound it), four for float rows.
+template <class P, int BS, int MINB>
+int launch_pair(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+  FastView F = make_view<P>(s);
+  F.dotp = dotp;
+  size_t smem = pair_smem<P>(F.D, F.n_coef);
+  auto kern = k_apply_pair<P, BS, MINB>;
+  ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem));
+  if (per_sm < 1) ED_INVALID("two-row kernel does not fit on an SM (%zu B shared)", smem);
+  uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)s->ctx->num_sms * per_sm, (F.D_up + 1) / 2);
+  kern<<<grid, BS, smem, st>>>(F, static_cast<const typename P::V*>(x), static_cast<typename P::V*>(y));
+  ED_LAUNCH_CHECK();
+  if (nparts) *nparts = (int)grid;
+  return ED_OK;
+}
+
+// FP64 and double-float: three 256-thread single-row blocks per SM (shared
+// memory and registers both bound it).  Float rows: two-row blocks, three per SM.
 template <class P>
 int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
-  if (sizeof(typename P::V) == 4) return launch_fast<P, 256, 4>(s, x, y, st, dotp, nparts);
-  return launch_fast<P, 256, 3>(s, x, y, st, dotp, nparts);
+  if constexpr (P::prec != ED_PREC_FP32) {
+    if (s->fast.pair) ED_INVALID("row kernel tables were built for another vector format");
+    return launch_fast<P, 256, 3>(s, x, y, st, dotp, nparts);
+  } else {
+    if (!s->fast.pair) ED_INVALID("row kernel tables were built for another vector format");
+    return launch_pair<P, 256, 3>(s, x, y, st, dotp, nparts);
+  }
 }
 
 }  // namespace
@@ -468,7 +793,7 @@ int build_fast(Sector* s) {
   const uint32_t D = s->dn.D;
   if (D < 512 || s->n_chunks > 1 || s->up.max_hops > (uint32_t)kList || s->max_mix > (uint32_t)kList)
     return ED_OK;
-  if (s->dn.max_hops > 255 || (uint64_t)D * elem_bytes(s->prec) >= (1ull << 19)) return ED_OK;
+  if (s->dn.max_hops > 255) return ED_OK;
   if (s->dn_move && s->M * s->M > kList) return ED_OK;
   // distinct down-hop matrix elements plus a zero used for padding
   std::vector<double> hv(s->dn.n_hops);
@@ -492,8 +817,14 @@ int build_fast(Sector* s) {
     zero_id = (int)coef.size();
     coef.push_back(0.0);
   }
-  size_t smem_max = std::max(fast_smem<PolF64>(D, (int)coef.size()), fast_smem<PolDF>(D, (int)coef.size()));
-  if (smem_max > 220 * 1024) return ED_OK;
+  // float rows run the two-row kernel, the other formats the single-row one;
+  // hop words address the staged row in bytes below 2^19
+  const bool pair = s->prec == ED_PREC_FP32;
+  const size_t vbytes = (pair ? 2 : 1) * elem_bytes(s->prec);
+  if ((uint64_t)D * vbytes >= (1ull << 19)) return ED_OK;
+  const int nc = (int)coef.size();
+  const size_t smem = pair ? pair_smem<PolF32>(D, nc) : std::max(fast_smem<PolF64>(D, nc), fast_smem<PolDF>(D, nc));
+  if (smem > 220 * 1024) return ED_OK;
   const bool mix_delta = s->dn_move && s->orb0 + s->M == s->n_s && s->M * s->M * (1 << s->M) <= kMaxDelta;
 
   // window-local order: inside each window of 128 ranks, longest hop list first
@@ -540,7 +871,25 @@ int build_fast(Sector* s) {
     rkey[u] = cmask.size() <= 12 ? k : 0;
   }
   std::iota(rorder.begin(), rorder.end(), 0u);
-  std::stable_sort(rorder.begin(), rorder.end(), [&](uint32_t a, uint32_t b) { return rkey[a] < rkey[b]; });
+  if (pair) {
+    // inside a component, rows with equal up-hop and mixed-list lengths sit
+    // next to each other, so the two rows of a pair pad their lists little
+    std::vector<uint32_t> uptr(Du + 1), mptr;
+    ED_TRY_CUDA(cudaMemcpy(uptr.data(), s->up.hop_ptr, sizeof(uint32_t) * (Du + 1), cudaMemcpyDeviceToHost));
+    if (s->mx_ptr) {
+      mptr.resize(Du + 1);
+      ED_TRY_CUDA(cudaMemcpy(mptr.data(), s->mx_ptr, sizeof(uint32_t) * (Du + 1), cudaMemcpyDeviceToHost));
+    }
+    auto lens = [&](uint32_t u) {
+      return std::make_pair(uptr[u + 1] - uptr[u], mptr.empty() ? 0u : mptr[u + 1] - mptr[u]);
+    };
+    std::stable_sort(rorder.begin(), rorder.end(), [&](uint32_t a, uint32_t b) {
+      if (rkey[a] != rkey[b]) return rkey[a] < rkey[b];
+      return lens(a) < lens(b);
+    });
+  } else {
+    std::stable_sort(rorder.begin(), rorder.end(), [&](uint32_t a, uint32_t b) { return rkey[a] < rkey[b]; });
+  }
 
   auto& f = s->fast;
   const int wbits = (s->n_chunks == 1) ? s->w_bits[0] : 0;
@@ -561,6 +910,7 @@ int build_fast(Sector* s) {
   ED_TRY_CUDA(cudaMemcpy(f.coef, coef.data(), sizeof(double) * f.n_coef, cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.row_order, rorder.data(), sizeof(uint32_t) * Du, cudaMemcpyHostToDevice));
   f.mix_delta = mix_delta;
+  f.pair = pair;
   if (mix_delta) {
     const int M = s->M, NP = 1 << M;
     std::vector<uint32_t> dbas(D), wpat(n_win, 0xffffffffu);
@@ -580,7 +930,7 @@ int build_fast(Sector* s) {
   }
   k_win_tables<<<(unsigned)((NE + 127) / 128), 128>>>(D, n_win, f.max_cnt, f.perm, s->dn.basis, s->dn.hop_ptr,
                                                       s->dn.hop_tgt, s->dn.hop_val, f.coef, f.n_coef, zero_id,
-                                                      (int)elem_bytes(s->prec), s->prec == ED_PREC_FP64 ? 8 : 8,
+                                                      (int)vbytes, pair ? 16 : 8,
                                                       f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo,
                                                       wbits, f.n_pat, f.dd, s->orb0, f.dpat);
   ED_LAUNCH_CHECK();

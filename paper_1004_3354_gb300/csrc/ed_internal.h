@@ -161,6 +161,11 @@ struct Sector {
     uint8_t* dpat = nullptr;        // [n_win*128] impurity pattern of each entry
     uint32_t* wpat = nullptr;       // [n_win] pattern shared by a whole window, or ~0u
     int32_t* mdelta = nullptr;      // [M*M][2^M] (shift << 1 | sign) or INT32_MIN
+    // two-row kernel (float vectors): rows are processed in pairs
+    // (row_order[2i], row_order[2i+1]) staged interleaved, and the hop words
+    // hold byte offsets into that interleaved row and into a table of 16-byte
+    // coefficient entries
+    bool pair = false;
   } fast;
   // stored CSR (optional)
   uint64_t csr_nnz = 0;
@@ -253,6 +258,32 @@ __device__ __forceinline__ void df_mac1(float2& acc, float2 c, float x) {
   two_sum(acc.x, p, s, t);
   acc.x = s;
   acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+}
+
+// Two independent double-float accumulators at once with the paired FP32
+// instructions (add/sub/mul/fma .f32x2): H = (hi0, hi1), L = (lo0, lo1) take
+// (Ch, Cl) * (Xh, Xl) lane-wise, each lane exactly as df_mac (or as df_mac1
+// when XLO is false and x is a plain float).
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
+template <bool XLO>
+__device__ __forceinline__ void df_mac2(float2& H, float2& L, float2 Ch, float2 Cl, float2 Xh, float2 Xl) {
+  const float2 P = __fmul2_rn(Ch, Xh);
+  float2 E = __ffma2_rn(Ch, Xh, make_float2(-P.x, -P.y));
+  if (XLO) E = __ffma2_rn(Ch, Xl, E);
+  E = __ffma2_rn(Cl, Xh, E);
+  const float2 S = __fadd2_rn(H, P);
+  const float2 BB = f2_sub(S, H);
+  const float2 T = __fadd2_rn(f2_sub(H, f2_sub(S, BB)), f2_sub(P, BB));
+  H = S;
+  L = __fadd2_rn(L, __fadd2_rn(T, E));
 }
 
 __device__ __forceinline__ float2 df_norm(float2 a) {

@@ -96,7 +96,8 @@ def sample_rows(dim, D_dn, k=2500, seed=3):
     return np.array(sorted(r for r in rows if 0 <= r < dim))
 
 
-# (name, model, n_up, n_dn, kernel chosen by default: 0 flat, 1 row-staged generic, 2 fast rows)
+# (name, model, n_up, n_dn, kernel chosen by default: 0 flat, 1 row-staged generic, 2 fast rows;
+# the fast path runs two rows per block (kernel 3) for FP32 vectors)
 SAMPLED = [
     ("C1 Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6, 2),
     ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7, 2),
@@ -105,7 +106,13 @@ SAMPLED = [
     ("Hubbard ring N_s=13 (7,6) K=13", lambda: W.hubbard_cluster(13, tp=0.1), 7, 6, 1),
     ("Kanamori impurity on low sites N_s=13 (6,7)", lambda: W.kanamori(13, seed=3, imp_first=True), 6, 7, 2),
     ("Kanamori 4 orbitals N_s=14 (7,5)", lambda: W.kanamori(14, seed=5, n_orb=4), 7, 5, 2),
+    ("Kanamori N_s=13 (1,6) odd row count", lambda: W.kanamori(13, seed=3), 1, 6, 2),
+    ("AIM N_s=13 (3,6) two-row pairs", lambda: W.aim(13, seed=4), 3, 6, 2),
 ]
+
+
+def fast_kernel(kern, prec):
+    return 3 if kern == 2 and prec == "fp32" else kern
 
 
 @pytest.mark.parametrize("generic", [False, True], ids=["default", "generic"])
@@ -119,7 +126,7 @@ def test_apply_sampled_rows(env, name, mk, nu, nd, kern, prec, generic):
     x = W.random_vector(dim, seed=2)
     xin = input_for(prec, x)
     flags = ed.ED_SECTOR_GENERIC if generic else 0
-    want = (1 if D_dn >= 1024 else 0) if generic else kern
+    want = (1 if D_dn >= 1024 else 0) if generic else fast_kernel(kern, prec)
     if prec == "fp32" and want == 1 and D_dn * 4 > 96 * 1024:
         want = 0
     y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, flags, expect_kernel=want)
@@ -138,7 +145,7 @@ def test_apply_n15_half_filling_sampled(env, prec):
     dim = 6435 * 6435
     x = W.random_vector(dim, seed=1)
     xin = input_for(prec, x)
-    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, expect_kernel=2)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, expect_kernel=fast_kernel(2, prec))
     rows = sample_rows(dim, 6435, k=1500)
     ref = osec.apply_rows(m, nu, nd, rows, xin)
     assert rel_err(y[rows], ref) <= TOL[prec]
