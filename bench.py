@@ -504,9 +504,10 @@ def run_serve(a):
 
 
 def run_solve15(a):
-    """The N_s=15 (7,8) sector: ground state (three-vector Lanczos) and the
-    continued-fraction G(i w_n) on 1024 Matsubara points at beta = 40, in FP64,
-    DF64 and FP32 vectors; the stored-CSR H*v (FP64) beside the matrix-free one."""
+    """The N_s=15 (7,8) sector: ground state (three-vector Lanczos), the
+    continued-fraction G(i w_n) on 1024 Matsubara points at beta = 40 and the
+    spectral function A(w) on 2001 real frequencies, in FP64, DF64 and FP32
+    vectors; the stored-CSR H*v (FP64) beside the matrix-free one."""
     import torch
     import paper_1004_3354_gb300 as ed
     import workloads as W
@@ -519,7 +520,7 @@ def run_solve15(a):
     ctx = ed.ed_ctx_create(0)
     out = {"metric": "N_s=15 ground state + G(i w_n): time and error per vector format", "n_gpus": 1,
            "data": "synthetic (seeded random bath)", "config": workload_config("fp64", dim), "results": {}}
-    ref_E, ref_G = None, None
+    ref_E, ref_G, ref_A = None, None, None
     for prec in ("fp64", "df64", "fp32"):
         p = ed.PREC_NAMES[prec]
         sec = ed.ed_sector_create(ctx, m, NUP, NDN, prec)
@@ -532,15 +533,25 @@ def run_solve15(a):
         G = ed.ed_greens_cf(ctx, m, prec, [(NUP, NDN, float(ev[0]), psi)], 40.0, 1024, orbital=m.orb0, spin=0,
                             depth=150)
         t2 = time.perf_counter()
+        # spectral function on the real axis: A(w) = -Im G(w + i 0.05) / pi, 2001 points in [-8, 8]
+        zr = np.linspace(-8.0, 8.0, 2001) + 0.05j
+        Gr = ed.ed_greens_cf_z(ctx, m, prec, [(NUP, NDN, float(ev[0]), psi)], zr, 40.0, orbital=m.orb0, spin=0,
+                               depth=150)
+        t3 = time.perf_counter()
+        A = -Gr.imag / np.pi
         ed.ed_sector_destroy(sec)
         del psi
         r = {"E0": float(ev[0]), "lanczos_steps": info.iters, "ground_state_s": t1 - t0,
-             "apply_ms_total": info.apply_ms, "greens_s": t2 - t1, "status": st}
+             "apply_ms_total": info.apply_ms, "greens_s": t2 - t1, "spectral_real_axis_s": t3 - t2,
+             "spectral_weight_in_window": float(np.trapezoid(A, zr.real) if hasattr(np, "trapezoid")
+                                                else np.trapz(A, zr.real)),
+             "status": st}
         if prec == "fp64":
-            ref_E, ref_G = float(ev[0]), G
+            ref_E, ref_G, ref_A = float(ev[0]), G, A
         else:
             r["rel_E0_err_vs_fp64"] = abs(float(ev[0]) - ref_E) / abs(ref_E)
             r["max_abs_G_err_vs_fp64"] = float(np.max(np.abs(G - ref_G)))
+            r["max_abs_A_err_vs_fp64"] = float(np.max(np.abs(A - ref_A)))
         out["results"][prec] = r
     # stored CSR vs matrix-free, FP64
     sec = ed.ed_sector_create(ctx, m, NUP, NDN, "fp64", ed.ED_SECTOR_CSR)

@@ -238,6 +238,17 @@ int ed_greens_cf(ed_ctx* ctx, const ed_model* model, int prec, int n_states,
                  const ed_state* states, double beta, int n_w, int orbital, int spin,
                  int depth, double boltz_cut, double* G, double* coeffs, void* stream);
 
+/* The same Green's function at n_z arbitrary complex frequencies z (host,
+ * 2*n_z doubles, re/im interleaved, every Im z > 0; ED_ERR_INVALID otherwise):
+ * G(z) = sum_nu w_nu [n+ / (z + E_nu - a_0 - ...) + n- / (z - E_nu + a_0 - ...)].
+ * With z = w + i eta it gives the real-frequency spectral function
+ * A(w) = -Im G(w + i eta) / pi that Figs. 3 and 5 plot; with z = i w_n it equals
+ * ed_greens_cf.  beta still sets the Boltzmann weights of the states.  G: host,
+ * 2*n_z doubles; coeffs and all other arguments as ed_greens_cf.  Synchronises. */
+int ed_greens_cf_z(ed_ctx* ctx, const ed_model* model, int prec, int n_states,
+                   const ed_state* states, double beta, int n_z, const double* z, int orbital,
+                   int spin, int depth, double boltz_cut, double* G, double* coeffs, void* stream);
+
 /* ------------------------------------------------------- batched sectors */
 typedef struct ed_batch ed_batch;
 

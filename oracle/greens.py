@@ -1,4 +1,7 @@
-"""Matsubara Green's function: Lehmann sum (Eq. 3) and Lanczos continued fractions.
+"""Green's function: Lehmann sum (Eq. 3) and Lanczos continued fractions, at the
+Matsubara points or at any complex frequency off the real axis (z = w + i eta
+gives the real-frequency spectral function A(w) = -Im G(w + i eta) / pi that
+Figs. 3 and 5 of the paper plot).
 
 Test infrastructure (see ``oracle/__init__``).
 
@@ -54,9 +57,10 @@ def op_matrix(n_s: int, n_up: int, n_dn: int, orbital: int, spin: int, dagger: b
 
 
 def lehmann(model, beta: float, n_w: int, orbital: int = 0, spin: int = fock.UP,
-            sectors=None) -> np.ndarray:
+            sectors=None, z=None) -> np.ndarray:
     """Eq. 3 (standard sign) summed over all eigenstates of the given sectors
-    (default: every sector) by full diagonalisation."""
+    (default: every sector) by full diagonalisation, at z = i w_n (n < n_w) or,
+    if given, at the complex frequencies z (n_w is then ignored)."""
     n = model.n_s
     if sectors is None:
         sectors = [(a, b) for a in range(n + 1) for b in range(n + 1)]
@@ -67,8 +71,8 @@ def lehmann(model, beta: float, n_w: int, orbital: int = 0, spin: int = fock.UP,
         eig[(a, b)] = (w, v)
     E0 = min(w.min() for w, _ in eig.values())
     Z = sum(np.exp(-beta * (w - E0)).sum() for w, _ in eig.values())
-    iw = 1j * matsubara(beta, n_w)
-    G = np.zeros(n_w, dtype=complex)
+    iw = 1j * matsubara(beta, n_w) if z is None else np.asarray(z, dtype=complex)
+    G = np.zeros(len(iw), dtype=complex)
     for (a, b), (w_nu, v_nu) in eig.items():
         C, tgt = op_matrix(n, a, b, orbital, spin, True)
         if C is None or tgt not in eig:
@@ -126,8 +130,9 @@ def cf_eval(z: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def greens_cf(model, states, beta: float, n_w: int, orbital: int = 0, spin: int = fock.UP,
               depth: int = 150, boltz_cut: float = 1e-5, reorth: bool = False,
-              return_parts: bool = False):
-    """Continued-fraction G(i w_n) from a list of states (n_up, n_dn, E, vector).
+              return_parts: bool = False, z=None):
+    """Continued-fraction G(i w_n) (or G(z) at the given complex z) from a list
+    of states (n_up, n_dn, E, vector).
 
     Z is the sum of e^{-beta (E - E_min)} over the states passed; states whose
     factor is below ``boltz_cut`` are left out of the sum over nu."""
@@ -135,8 +140,8 @@ def greens_cf(model, states, beta: float, n_w: int, orbital: int = 0, spin: int 
     E0 = E.min()
     fac = np.exp(-beta * (E - E0))
     Z = fac.sum()
-    iw = 1j * matsubara(beta, n_w)
-    G = np.zeros(n_w, dtype=complex)
+    iw = 1j * matsubara(beta, n_w) if z is None else np.asarray(z, dtype=complex)
+    G = np.zeros(len(iw), dtype=complex)
     parts = []
     n = model.n_s
     Hcache = {}
@@ -165,3 +170,8 @@ def greens_cf(model, states, beta: float, n_w: int, orbital: int = 0, spin: int 
             else:
                 G += w * n2 * (-cf_eval(-(iw - En), a, b))
     return (G, parts) if return_parts else G
+
+
+def spectral(G: np.ndarray) -> np.ndarray:
+    """A(w) = -Im G(w + i eta) / pi from G on the line z = w + i eta."""
+    return -np.imag(G) / np.pi

@@ -115,6 +115,9 @@ _SIGS = {
     "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
                                C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
+    "ed_greens_cf_z": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
+                                 C.c_double, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_batch_create": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                   C.POINTER(C.c_void_p)]),
     "ed_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -304,6 +307,28 @@ def ed_greens_cf(ctx, model, prec, states, beta, n_w, orbital=0, spin=ED_SPIN_UP
                              int(n_w), int(orbital), int(spin), int(depth), float(boltz_cut),
                              G.ctypes.data_as(C.c_void_p),
                              None if co is None else co.ctypes.data_as(C.c_void_p), _stream(stream)))
+    Gc = G[0::2] + 1j * G[1::2]
+    if want_coeffs:
+        return Gc, co.reshape(len(states) * 2, 2 + 2 * depth)
+    return Gc
+
+
+def ed_greens_cf_z(ctx, model, prec, states, z, beta, orbital=0, spin=ED_SPIN_UP, depth=150,
+                   boltz_cut=1e-5, want_coeffs=False, stream=None):
+    """G(z) at complex frequencies z (array, every Im z > 0), e.g. z = w + i eta
+    for the spectral function A(w) = -Im G / pi.  states as in ed_greens_cf."""
+    mm = model if isinstance(model, Model) else Model(model)
+    arr = (ed_state * len(states))()
+    for i, (nu, nd, E, v) in enumerate(states):
+        arr[i] = ed_state(int(nu), int(nd), float(E), v.data_ptr())
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128)).view(np.float64)
+    n_z = zz.size // 2
+    G = np.zeros(2 * n_z, dtype=np.float64)
+    co = np.zeros(len(states) * 2 * (2 + 2 * depth), dtype=np.float64) if want_coeffs else None
+    check(lib().ed_greens_cf_z(ctx, C.byref(mm.c), PREC_NAMES.get(prec, prec), len(states), arr, float(beta),
+                               int(n_z), zz.ctypes.data_as(C.c_void_p), int(orbital), int(spin), int(depth),
+                               float(boltz_cut), G.ctypes.data_as(C.c_void_p),
+                               None if co is None else co.ctypes.data_as(C.c_void_p), _stream(stream)))
     Gc = G[0::2] + 1j * G[1::2]
     if want_coeffs:
         return Gc, co.reshape(len(states) * 2, 2 + 2 * depth)

@@ -66,8 +66,8 @@ int convert_async(const void* src, int sp, void* dst, int dp, uint64_t n, cudaSt
 int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
                 cudaStream_t st);
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
-                  int n_w, int orbital, int spin, int depth, double boltz_cut, double* G, double* coeffs,
-                  cudaStream_t st);
+                  int n_w, const double* z, int orbital, int spin, int depth, double boltz_cut, double* G,
+                  double* coeffs, cudaStream_t st);
 
 namespace {
 
@@ -357,7 +357,18 @@ int ed_greens_cf(ed_ctx* ctx, const ed_model* model, int prec, int n_states, con
   ED_GUARD_BEGIN
   if (!ctx || !model) ED_INVALID("NULL argument");
   ED_TRY_CUDA(cudaSetDevice(ctx->c.device));
-  return greens_cf_run(&ctx->c, model, prec, n_states, states, beta, n_w, orbital, spin, depth, boltz_cut, G,
+  return greens_cf_run(&ctx->c, model, prec, n_states, states, beta, n_w, nullptr, orbital, spin, depth,
+                       boltz_cut, G, coeffs, as_stream(stream));
+  ED_GUARD_END
+}
+
+int ed_greens_cf_z(ed_ctx* ctx, const ed_model* model, int prec, int n_states, const ed_state* states,
+                   double beta, int n_z, const double* z, int orbital, int spin, int depth, double boltz_cut,
+                   double* G, double* coeffs, void* stream) {
+  ED_GUARD_BEGIN
+  if (!ctx || !model || !z) ED_INVALID("NULL argument");
+  ED_TRY_CUDA(cudaSetDevice(ctx->c.device));
+  return greens_cf_run(&ctx->c, model, prec, n_states, states, beta, n_z, z, orbital, spin, depth, boltz_cut, G,
                        coeffs, as_stream(stream));
   ED_GUARD_END
 }

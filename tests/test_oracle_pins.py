@@ -55,6 +55,48 @@ def check_u0_greens():
     assert np.max(np.abs(G - ref)) < 1e-12, np.max(np.abs(G - ref))
 
 
+def check_u0_greens_real_axis():
+    """Non-interacting limit off the real axis: G(w + i eta) = [((w + i eta) - T)^-1]_00
+    (Lehmann over all sectors), and G(z*) = G(z)* for a real Hamiltonian."""
+    m = W.aim(4, seed=6, U=0.0)
+    z = np.linspace(-3.0, 3.0, 41) + 0.05j
+    G = greens.lehmann(m, 9.0, 0, orbital=0, spin=fock.UP, z=z)
+    ref = np.array([np.linalg.inv(zz * np.eye(4) - m.T)[0, 0] for zz in z])
+    assert np.max(np.abs(G - ref)) < 1e-12, np.max(np.abs(G - ref))
+    Gc = greens.lehmann(m, 9.0, 0, orbital=0, spin=fock.UP, z=np.conj(z))
+    assert np.max(np.abs(Gc - np.conj(G))) < 1e-12
+
+
+def check_spectral_sum_rule():
+    """A(w) = -Im G(w + i eta) / pi is non-negative and integrates to <{c, c+}> = 1
+    (each pole is a Lorentzian of unit total weight; the tails beyond |w| = W
+    carry about 2 eta / (pi W) of it)."""
+    m = W.aim(4, seed=2, U=2.0)
+    eta, Wd = 0.05, 400.0
+    w = np.linspace(-Wd, Wd, 160001)
+    G = greens.lehmann(m, 10.0, 0, orbital=0, spin=fock.UP, z=w + 1j * eta)
+    A = greens.spectral(G)
+    assert A.min() > 0.0
+    tot = np.trapezoid(A, w) if hasattr(np, "trapezoid") else np.trapz(A, w)
+    assert abs(tot - (1.0 - 2 * eta / (np.pi * Wd))) < 2e-4, tot
+
+
+def check_cf_vs_lehmann_real_axis():
+    """CF over all eigenstates at full depth == Lehmann at z = w + i eta (interacting AIM)."""
+    m = W.aim(4, seed=11, U=2.5)
+    beta = 5.0
+    states = []
+    for nu in range(5):
+        for nd in range(5):
+            H = sector.build_csr(m, nu, nd).toarray()
+            w, v = np.linalg.eigh(H)
+            states += [(nu, nd, w[i], v[:, i]) for i in range(len(w))]
+    z = np.linspace(-4.0, 4.0, 33) + 0.1j
+    Gcf = greens.greens_cf(m, states, beta, 0, 0, fock.UP, depth=64, boltz_cut=0.0, reorth=True, z=z)
+    Gl = greens.lehmann(m, beta, 0, 0, fock.UP, z=z)
+    assert np.max(np.abs(Gcf - Gl)) < 1e-10, np.max(np.abs(Gcf - Gl))
+
+
 def multiset(vals, tol=1e-9):
     vals = np.sort(np.asarray(vals))
     out = []
@@ -227,6 +269,7 @@ def check_row_sampling():
 PINS = [check_two_site_hubbard, check_u0_ground_energy, check_u0_greens, check_t2g_multiplets,
         check_hermitian, check_conservation_and_blocks, check_particle_hole, check_spin_symmetry,
         check_su2_inclusion, check_cf_vs_lehmann, check_sum_rules, check_fig1_csr,
+        check_u0_greens_real_axis, check_spectral_sum_rule, check_cf_vs_lehmann_real_axis,
         check_sector_dims, check_tiers_agree, check_row_sampling]
 
 
