@@ -48,7 +48,7 @@ def args_parse(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15"],
+    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15", "lowest8"],
                    help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12; "
                         "serve: Poisson stream of impurity solves, N_s in 10..16; "
                         "solve15: N_s=15 ground state + G(i w_n) per vector format, and the stored-CSR H*v")
@@ -580,6 +580,54 @@ def run_solve15(a):
     print(json.dumps(out), flush=True)
 
 
+def run_lowest8(a):
+    """Eight lowest states (k = 8, DF64 vectors, tol 1e-10): the N_s=15 (7,8)
+    sector by Lanczos with a full CGS2 basis and by thick-restart Lanczos with a
+    40-vector basis; the N_s=16 (8,8) sector (dim 165,636,900, 1.3 GB per
+    vector) by thick restart only, whose bounded basis fits in HBM where a full
+    basis of a few hundred vectors would not."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    import workloads as W
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    ctx = ed.ed_ctx_create(0)
+    out = {"metric": "8 lowest states: time, H*v products and device memory, full basis vs thick restart",
+           "n_gpus": 1, "data": "synthetic (seeded random bath)", "vector_format": "df64", "results": {}}
+    runs = [(15, 7, 8, "full_basis"), (15, 7, 8, "thick_restart"), (16, 8, 8, "thick_restart")]
+    ref = {}
+    for ns, nu, nd, how in runs:
+        m = W.kanamori(ns, seed=SEED)
+        sec = ed.ed_sector_create(ctx, m, nu, nd, "df64")
+        dim = W.sector_dim(ns, nu, nd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if how == "full_basis":
+            # the full basis is allocated for max_iter + 1 vectors (plus the work vector)
+            ev, info, st = ed.ed_lanczos(sec, k=8, tol=1e-10, max_iter=320, check_every=10,
+                                         allow_not_converged=True)
+            r = {"iters": info.iters, "basis_bytes": (320 + 2) * dim * 8,
+                 "basis_bytes_used": (info.iters + 2) * dim * 8}
+        else:
+            ev, info, st = ed.ed_lanczos_tr(sec, k=8, tol=1e-10, max_basis=40, keep=20, max_iter=3000,
+                                            check_every=5, allow_not_converged=True)
+            r = {"iters": info.iters, "restarts": info.restarts, "basis_bytes": info.basis_bytes}
+        el = time.perf_counter() - t0
+        r.update({"n_s": ns, "sector": [nu, nd], "dim": dim, "seconds": el, "apply_ms_total": info.apply_ms,
+                  "status": st, "n_converged": info.n_converged, "evals": [float(v) for v in ev],
+                  "max_residual": float(max(info.residual[:8]))})
+        if ns in ref:
+            r["max_abs_eval_diff_vs_full_basis"] = float(np.max(np.abs(np.array(ev) - ref[ns])))
+        else:
+            ref[ns] = np.array(ev)
+        out["results"][f"ns{ns}_{how}"] = r
+        ed.ed_sector_destroy(sec)
+    ed.ed_ctx_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = args_parse()
     if a.impl == "reference":
@@ -590,5 +638,7 @@ if __name__ == "__main__":
         run_serve(a)
     elif a.workload == "solve15":
         run_solve15(a)
+    elif a.workload == "lowest8":
+        run_lowest8(a)
     else:
         run_ours(a)

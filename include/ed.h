@@ -218,6 +218,47 @@ typedef struct ed_lanczos_info {
 int ed_lanczos(ed_sector* s, const ed_lanczos_opts* opts, double* evals,
                void* evecs, ed_lanczos_info* info, void* stream);
 
+/* ------------------------------------------------ thick-restart Lanczos */
+#define ED_MAX_BASIS 128
+
+typedef struct ed_trlan_opts {
+  int k;               /* lowest eigenpairs wanted (1..ED_MAX_K) */
+  double tol;          /* converged when beta |y_last,i| <= tol * max(1, |theta_i|) */
+  int max_basis;       /* basis size m before a restart: k + 2 <= m <= ED_MAX_BASIS (or >= dim) */
+  int keep;            /* Ritz vectors kept at a restart, k..m-2; 0 chooses (m + k) / 2 */
+  int max_iter;        /* H*v products at most, over all restarts */
+  int check_every;     /* steps between projected eigen-solves (>= 1); a full basis always checks */
+  uint64_t seed;       /* start vector seed when v0 == NULL */
+  const void* v0;      /* optional device start vector (sector format), NULL = seeded */
+} ed_trlan_opts;
+
+typedef struct ed_trlan_info {
+  int iters;                    /* H*v products */
+  int restarts;                 /* thick restarts */
+  int n_converged;              /* leading eigenvalues meeting tol */
+  double residual[ED_MAX_K];    /* Ritz residual estimates */
+  double apply_ms;              /* device time in H*v (CUDA events) */
+  double total_ms;              /* wall time of the call */
+  size_t basis_bytes;           /* device bytes of basis, work vector and rotation target */
+} ed_trlan_info;
+
+/* Lowest k eigenvalues (host, ascending; NaN past the sector dimension) and,
+ * if evecs != NULL, the Ritz vectors (device, k consecutive vectors of dim
+ * elements in the sector's format) by thick-restart Lanczos with full CGS2
+ * reorthogonalisation.  The paper's solver is implicitly restarted Arnoldi
+ * (abstract, Sec. 3); for symmetric H a restart with the unwanted Ritz values
+ * as exact shifts keeps the span of the wanted Ritz vectors plus the residual
+ * direction, which is what this keeps explicitly, so the device memory is
+ * bounded by (max_basis + 2 + keep) vectors however many steps convergence
+ * takes.  The projected eigenproblem runs on the device (one-block Jacobi).
+ * An exhausted Krylov space with fewer than k values continues from a seeded
+ * direction orthogonal to the basis (degenerate multiplets).  Returns
+ * ED_ERR_NOT_CONVERGED with the current estimates after max_iter products;
+ * ED_ERR_INVALID for arguments outside the ranges above; ED_ERR_OOM when the
+ * basis does not fit the context budget.  Synchronises. */
+int ed_lanczos_tr(ed_sector* s, const ed_trlan_opts* opts, double* evals, void* evecs,
+                  ed_trlan_info* info, void* stream);
+
 /* ------------------------------------------------------- Green's function */
 typedef struct ed_state {
   int n_up, n_dn;     /* sector of the state */

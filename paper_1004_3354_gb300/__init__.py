@@ -60,6 +60,17 @@ class ed_lanczos_info(C.Structure):
                 ("apply_ms", C.c_double), ("total_ms", C.c_double)]
 
 
+class ed_trlan_opts(C.Structure):
+    _fields_ = [("k", C.c_int), ("tol", C.c_double), ("max_basis", C.c_int), ("keep", C.c_int),
+                ("max_iter", C.c_int), ("check_every", C.c_int), ("seed", C.c_uint64), ("v0", C.c_void_p)]
+
+
+class ed_trlan_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("n_converged", C.c_int),
+                ("residual", C.c_double * ED_MAX_K), ("apply_ms", C.c_double), ("total_ms", C.c_double),
+                ("basis_bytes", C.c_size_t)]
+
+
 class ed_batch_info(C.Structure):
     _fields_ = [("steps", C.c_int), ("graph_replays", C.c_int), ("n_sectors", C.c_int), ("total_ms", C.c_double)]
 
@@ -112,6 +123,8 @@ _SIGS = {
     "ed_dot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ed_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                              C.POINTER(ed_lanczos_info), C.c_void_p]),
+    "ed_lanczos_tr": (C.c_int, [C.c_void_p, C.POINTER(ed_trlan_opts), C.c_void_p, C.c_void_p,
+                                C.POINTER(ed_trlan_info), C.c_void_p]),
     "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
                                C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p,
                                C.c_void_p, C.c_void_p]),
@@ -288,6 +301,19 @@ def ed_lanczos(sec, k=1, tol=1e-12, max_iter=300, check_every=10, seed=1, v0=Non
     info = ed_lanczos_info()
     st = lib().ed_lanczos(sec, C.byref(o), ev.ctypes.data_as(C.c_void_p), _ptr(evecs), C.byref(info),
                           _stream(stream))
+    check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return ev, info, st
+
+
+def ed_lanczos_tr(sec, k=1, tol=1e-12, max_basis=40, keep=0, max_iter=2000, check_every=5, seed=1, v0=None,
+                  evecs=None, stream=None, allow_not_converged=False):
+    """Thick-restart Lanczos.  Returns (evals ndarray[k], info, status)."""
+    o = ed_trlan_opts(int(k), float(tol), int(max_basis), int(keep), int(max_iter), int(check_every), int(seed),
+                      None if v0 is None else v0.data_ptr())
+    ev = np.zeros(k, dtype=np.float64)
+    info = ed_trlan_info()
+    st = lib().ed_lanczos_tr(sec, C.byref(o), ev.ctypes.data_as(C.c_void_p), _ptr(evecs), C.byref(info),
+                             _stream(stream))
     check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return ev, info, st
 

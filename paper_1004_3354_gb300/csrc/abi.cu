@@ -65,6 +65,8 @@ void dev_free(Ctx* c, void* p, size_t bytes) {
 int convert_async(const void* src, int sp, void* dst, int dp, uint64_t n, cudaStream_t st);
 int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs, ed_lanczos_info* info,
                 cudaStream_t st);
+int trlan_run(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed_trlan_info* info,
+              cudaStream_t st);
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
                   int n_w, const double* z, int orbital, int spin, int depth, double boltz_cut, double* G,
                   double* coeffs, cudaStream_t st);
@@ -348,6 +350,17 @@ int ed_lanczos(ed_sector* h, const ed_lanczos_opts* opts, double* evals, void* e
   if (info) std::memset(info, 0, sizeof(*info));
   ED_TRY_CUDA(cudaSetDevice(h->s.ctx->device));
   return lanczos_run(&h->s, opts, evals, evecs, info, as_stream(stream));
+  ED_GUARD_END
+}
+
+int ed_lanczos_tr(ed_sector* h, const ed_trlan_opts* opts, double* evals, void* evecs, ed_trlan_info* info,
+                  void* stream) {
+  ED_GUARD_BEGIN
+  if (!h || !opts || !evals) ED_INVALID("NULL argument");
+  if (opts->max_iter < 1) ED_INVALID("max_iter must be >= 1");
+  if (info) std::memset(info, 0, sizeof(*info));
+  ED_TRY_CUDA(cudaSetDevice(h->s.ctx->device));
+  return trlan_run(&h->s, opts, evals, evecs, info, as_stream(stream));
   ED_GUARD_END
 }
 

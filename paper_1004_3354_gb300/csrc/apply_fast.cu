@@ -112,9 +112,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ uint32_t sel4(const uint4& v, int e) {
   return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
-__device__ __forceinline__ uint32_t sel4(const uchar4& v, int e) {
-  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
 
 template <class P, int BS, int MINB>
 __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typename P::V* __restrict__ x,

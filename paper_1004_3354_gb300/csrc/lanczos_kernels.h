@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const V* __restrict__ x, co
   if (threadIdx.x == 0) partial[blockIdx.x] = to_d(acc);
 }
 
-// Multi-dot: partial[k * nb + b] = block b's share of <V_k, w>, k < nvec.
+// Multi-dot of the chunk k0 .. k0 + KB - 1: partial[q * nb + b] = block b's
+// share of <V_{k0+q}, w>.
 template <class V, int KB>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const V* __restrict__ Vb, uint64_t stride, int k0,
                                                           int nvec, const V* __restrict__ w, uint64_t n,
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const V* __restrict__ 
   }
   for (int q = 0; q < kn; ++q) {
     A r = block_reduce(acc[q], sh);
-    if (threadIdx.x == 0) partial[(uint64_t)(k0 + q) * gridDim.x + blockIdx.x] = to_d(r);
+    if (threadIdx.x == 0) partial[(uint64_t)q * gridDim.x + blockIdx.x] = to_d(r);
   }
 }
 
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(kRedThreads) k_finish(const double* __restrict
       break;
     }
     case OP_NEGH:
-      c.h_d[o] = -v;
-      c.h_f[o] = df_from_double(-v);
+      c.h_d[slot + o] = -v;
+      c.h_f[slot + o] = df_from_double(-v);
       break;
     case OP_NORM_INV: {
       double b = sqrt(fmax(v, 0.0));
@@ -393,16 +394,19 @@ int dot_to(Work<V>& W, const V* x, const V* y, int op, int slot, double thr = 0.
   return ED_OK;
 }
 
-// CGS2 against basis vectors [0, nvec): twice h = V^T w, w -= V h.
+// CGS2 against basis vectors [0, nvec): twice h = V^T w, w -= V h.  The
+// projections are reduced eight at a time, so every chunk runs on the full
+// grid whatever the basis size.
 template <class V>
 int cgs2(Work<V>& W, const V* Vb, uint64_t stride, int nvec, V* w) {
   if (nvec <= 0) return ED_OK;
-  int nb = (int)std::min<uint64_t>(W.grid, (uint64_t)kRedSlots / (uint64_t)nvec);
-  if (nb < 1) ED_INVALID("too many basis vectors for the reduction scratch (%d)", nvec);
+  constexpr int KB = 8;
+  const int nb = (int)std::min<uint64_t>(W.grid, (uint64_t)kRedSlots / KB);
   for (int pass = 0; pass < 2; ++pass) {
-    for (int k0 = 0; k0 < nvec; k0 += 8)
-      k_multidot<V, 8><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
-    k_finish<<<nvec, kRedThreads, 0, W.st>>>(W.partial, nb, OP_NEGH, 0, W.c, 0.0);
+    for (int k0 = 0; k0 < nvec; k0 += KB) {
+      k_multidot<V, KB><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
+      k_finish<<<std::min(KB, nvec - k0), kRedThreads, 0, W.st>>>(W.partial, nb, OP_NEGH, k0, W.c, 0.0);
+    }
     k_multi_axpy<V><<<W.grid, 256, 0, W.st>>>(Vb, stride, nvec, w, W.n, W.c);
     ED_LAUNCH_CHECK();
   }
