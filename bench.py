@@ -47,6 +47,7 @@ def args_parse(argv=None):
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
+    p.add_argument("--no-autotune", action="store_true", help="time the untuned default H*v variant")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15", "lowest8"],
                    help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12; "
@@ -164,14 +165,19 @@ def cpu_baseline(model, x, prec, seconds):
 
 
 def row_kernel(prec):
-    """The fast row kernel that ed_apply_h launches for this vector format."""
+    """The fast row kernel that ed_apply_h launches, untuned, for this vector format."""
     return "k_apply_pair" if prec == "fp32" else "k_apply_win"
 
 
-def traffic_for(kernel_src_sha, prec):
+def row_kernel_of(kernel_id):
+    """Kernel name of an ed_sector_info / ed_tune_result kernel id."""
+    return {2: "k_apply_win", 3: "k_apply_pair"}.get(kernel_id, f"generic_{kernel_id}")
+
+
+def traffic_for(kernel_src_sha, prec, kernel=None):
     """DRAM bytes per launch of the row kernel from the committed ncu summary,
     only if it was captured from the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"{row_kernel(prec)}_{prec}_n15_traffic.txt")
+    p = os.path.join(ROOT, "profiles", f"{kernel or row_kernel(prec)}_{prec}_n15_traffic.txt")
     try:
         kv = dict(line.split(":", 1) for line in open(p) if ":" in line)
     except Exception:
@@ -226,6 +232,14 @@ def run_ours(a):
 
     ctx = ed.ed_ctx_create(local)
     sec = ed.ed_sector_create(ctx, model, NUP, NDN, a.prec)
+    tuned = None
+    if not a.no_autotune:
+        r = ed.ed_sector_autotune(sec, reps=5)
+        tuned = {"chosen": r.chosen, "candidates": [
+            {"kernel": row_kernel_of(r.kernel[i]), "block": r.block[i], "min_blocks_per_sm": r.min_blocks[i],
+             "ms": round(r.ms[i], 5) if r.ms[i] > 0 else None} for i in range(r.n_candidates)]}
+    variant = ed.ed_sector_get_variant(sec)
+    kernel_name = row_kernel_of(ed.ed_sector_get_info(sec).kernel)
     p = ed.PREC_NAMES[a.prec]
     epv = ed.elems_per_value(p)
     tdt = ed.torch_dtype(p)
@@ -295,6 +309,8 @@ def run_ours(a):
             if q == a.prec:
                 continue
             s2 = ed.ed_sector_create(ctx, model, NUP, NDN, q)
+            if not a.no_autotune:
+                ed.ed_sector_autotune(s2, reps=3)
             qp = ed.PREC_NAMES[q]
             xq = torch.empty(dim * ed.elems_per_value(qp), dtype=ed.torch_dtype(qp), device="cuda")
             ed.ed_convert(x, p, xq, qp, dim)
@@ -311,7 +327,8 @@ def run_ours(a):
             torch.cuda.synchronize()
             msq = s0.elapsed_time(s1) / n_q
             extras[q] = {"ms_per_apply": msq, "GB/s": alg_bytes(q, dim) / (msq * 1e-3) / 1e9,
-                         "kernel": row_kernel(q)}
+                         "kernel": row_kernel_of(ed.ed_sector_get_info(s2).kernel),
+                         "variant": ed.ed_sector_get_variant(s2)}
             del xq, yq
             ed.ed_sector_destroy(s2)
 
@@ -327,12 +344,12 @@ def run_ours(a):
         "data": "synthetic (seeded random bath)", "config": workload_config(a.prec, dim),
         "pct_hbm_peak": round(100 * value / world / peak, 2),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic_for(sha, a.prec),
-                     "kernel": row_kernel(a.prec), "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "frac": round(achieved / peak, 4), "traffic": traffic_for(sha, a.prec, kernel_name),
+                     "kernel": kernel_name, "variant": variant, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
                      "apply_src_sha": sha},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
-        "clocks": clk, "nnz_per_row": round(info.nnz_per_row, 3), "other_formats": extras,
+        "clocks": clk, "nnz_per_row": round(info.nnz_per_row, 3), "other_formats": extras, "autotune": tuned,
     }
     ed.ed_sector_destroy(sec)
     ed.ed_ctx_destroy(ctx)

@@ -218,6 +218,45 @@ typedef struct ed_lanczos_info {
 int ed_lanczos(ed_sector* s, const ed_lanczos_opts* opts, double* evals,
                void* evecs, ed_lanczos_info* info, void* stream);
 
+/* -------------------------------------------------------------- autotuner */
+#define ED_MAX_TUNE 16
+
+typedef struct ed_tune_result {
+  int n_candidates;               /* variants tried, in the order of the arrays */
+  int chosen;                     /* index of the fastest, now the sector's H*v; -1: nothing to choose */
+  int kernel[ED_MAX_TUNE];        /* 2: one up string per block, 3: two up strings per block */
+  int block[ED_MAX_TUNE];         /* threads per block */
+  int min_blocks[ED_MAX_TUNE];    /* blocks per SM the register budget is sized for */
+  double ms[ED_MAX_TUNE];         /* median device time of one H*v; -1 where it does not apply or fit */
+} ed_tune_result;
+
+/* Autotuner of the matrix-free H*v (the hot loop of Sec. 3's iterative
+ * solvers; the paper has no tuner): times every variant of the fast row
+ * kernel that applies to this sector -- one or two up strings per block, times
+ * the launch shapes (threads per block, blocks per SM) -- `reps` times each
+ * (median, CUDA events, after a warm-up) on internal random vectors, makes the
+ * fastest the sector's H*v, and records it in the context's cache under the
+ * sector's shape (format, sizes, hop counts), so that sectors of the same shape
+ * created later start with it.  All variants compute the same y bit for bit.
+ * Sectors without the fast kernel (ED_SECTOR_GENERIC, very short rows) have
+ * nothing to tune: n_candidates = 0, chosen = -1.  Allocates two vectors for
+ * the duration of the call.  Synchronises. */
+int ed_sector_autotune(ed_sector* s, int reps, ed_tune_result* out, void* stream);
+
+/* Choose the H*v variant by index (as in ed_tune_result), or -1 for the
+ * untuned default.  ED_ERR_INVALID if the variant does not apply.
+ * ed_sector_get_variant reports the variant in use (-1: the untuned default,
+ * also for sectors without the fast kernel). */
+int ed_sector_set_variant(ed_sector* s, int variant);
+int ed_sector_get_variant(const ed_sector* s, int* variant);
+
+/* Save the context's autotune cache as JSON (format "libedgb-autotune-1",
+ * with the GPU's name), or merge a saved one into it; entries saved on another
+ * GPU model are skipped (n_loaded counts the entries taken).  ED_ERR_INVALID
+ * for unreadable or malformed files. */
+int ed_tune_cache_save(ed_ctx* ctx, const char* path);
+int ed_tune_cache_load(ed_ctx* ctx, const char* path, int* n_loaded);
+
 /* ------------------------------------------------ thick-restart Lanczos */
 #define ED_MAX_BASIS 128
 

@@ -71,6 +71,15 @@ class ed_trlan_info(C.Structure):
                 ("basis_bytes", C.c_size_t)]
 
 
+ED_MAX_TUNE = 16
+
+
+class ed_tune_result(C.Structure):
+    _fields_ = [("n_candidates", C.c_int), ("chosen", C.c_int), ("kernel", C.c_int * ED_MAX_TUNE),
+                ("block", C.c_int * ED_MAX_TUNE), ("min_blocks", C.c_int * ED_MAX_TUNE),
+                ("ms", C.c_double * ED_MAX_TUNE)]
+
+
 class ed_batch_info(C.Structure):
     _fields_ = [("steps", C.c_int), ("graph_replays", C.c_int), ("n_sectors", C.c_int), ("total_ms", C.c_double)]
 
@@ -123,6 +132,11 @@ _SIGS = {
     "ed_dot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ed_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                              C.POINTER(ed_lanczos_info), C.c_void_p]),
+    "ed_sector_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ed_tune_result), C.c_void_p]),
+    "ed_sector_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "ed_sector_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "ed_tune_cache_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "ed_tune_cache_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int)]),
     "ed_lanczos_tr": (C.c_int, [C.c_void_p, C.POINTER(ed_trlan_opts), C.c_void_p, C.c_void_p,
                                 C.POINTER(ed_trlan_info), C.c_void_p]),
     "ed_greens_cf": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_int, C.POINTER(ed_state),
@@ -303,6 +317,34 @@ def ed_lanczos(sec, k=1, tol=1e-12, max_iter=300, check_every=10, seed=1, v0=Non
                           _stream(stream))
     check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return ev, info, st
+
+
+def ed_sector_autotune(sec, reps=5, stream=None):
+    """Time the fast H*v variants of the sector and keep the fastest; returns
+    the ed_tune_result (candidates, times, chosen index)."""
+    r = ed_tune_result()
+    check(lib().ed_sector_autotune(sec, int(reps), C.byref(r), _stream(stream)))
+    return r
+
+
+def ed_sector_set_variant(sec, variant):
+    check(lib().ed_sector_set_variant(sec, int(variant)))
+
+
+def ed_sector_get_variant(sec):
+    v = C.c_int(-1)
+    check(lib().ed_sector_get_variant(sec, C.byref(v)))
+    return v.value
+
+
+def ed_tune_cache_save(ctx, path):
+    check(lib().ed_tune_cache_save(ctx, os.fsencode(path)))
+
+
+def ed_tune_cache_load(ctx, path):
+    n = C.c_int(0)
+    check(lib().ed_tune_cache_load(ctx, os.fsencode(path), C.byref(n)))
+    return n.value
 
 
 def ed_lanczos_tr(sec, k=1, tol=1e-12, max_basis=40, keep=0, max_iter=2000, check_every=5, seed=1, v0=None,

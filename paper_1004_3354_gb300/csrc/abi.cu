@@ -67,6 +67,9 @@ int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs,
                 cudaStream_t st);
 int trlan_run(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed_trlan_info* info,
               cudaStream_t st);
+int autotune(Sector* s, int reps, ed_tune_result* out, cudaStream_t st);
+int tune_cache_save(Ctx* c, const char* path);
+int tune_cache_load(Ctx* c, const char* path, int* n_loaded);
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
                   int n_w, const double* z, int orbital, int spin, int depth, double boltz_cut, double* G,
                   double* coeffs, cudaStream_t st);
@@ -166,6 +169,7 @@ int ed_ctx_create(int device, size_t hbm_budget, ed_ctx** out) {
     ED_INVALID("device %d is sm_%d%d; this library is built for sm_103a", device, prop.major, prop.minor);
   }
   c.num_sms = prop.multiProcessorCount;
+  c.device_name = prop.name;
   c.smem_optin = prop.sharedMemPerBlockOptin;
   int st = dev_alloc_n(&c, &c.d_binom, 33 * 33);
   if (st == ED_OK) st = dev_alloc_n(&c, &c.d_red, kRedSlots);
@@ -215,6 +219,7 @@ int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn, int
   ed_sector* h = new ed_sector();
   int st = build_sector(&ctx->c, model, n_up, n_dn, prec, &h->s);
   if (st == ED_OK && !(flags & ED_SECTOR_GENERIC)) st = build_fast(&h->s);
+  if (st == ED_OK) tune_apply_cached(&h->s);
   if (st == ED_OK && (flags & ED_SECTOR_CSR)) st = build_csr(&h->s);
   if (st != ED_OK) {
     free_sector(&h->s);
@@ -263,7 +268,9 @@ int ed_sector_get_info(const ed_sector* h, ed_sector_info* out) {
       mix = (double)s.n_mix / s.up.D * (num / den);
     }
   }
-  out->kernel = s.fast.ok ? (s.fast.pair ? 3 : 2) : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
+  int fk = 0, fb = 0, fm = 0;
+  if (s.fast.ok) fast_variant_info(fast_variant_applies(&s, s.tune) ? s.tune : fast_default_variant(&s), &fk, &fb, &fm);
+  out->kernel = s.fast.ok ? fk : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
   out->nnz_per_row = 1.0 + (double)s.dn.n_hops / std::max<uint32_t>(s.dn.D, 1) +
                      (double)s.up.n_hops / std::max<uint32_t>(s.up.D, 1) + mix;
   return ED_OK;
@@ -350,6 +357,49 @@ int ed_lanczos(ed_sector* h, const ed_lanczos_opts* opts, double* evals, void* e
   if (info) std::memset(info, 0, sizeof(*info));
   ED_TRY_CUDA(cudaSetDevice(h->s.ctx->device));
   return lanczos_run(&h->s, opts, evals, evecs, info, as_stream(stream));
+  ED_GUARD_END
+}
+
+int ed_sector_autotune(ed_sector* h, int reps, ed_tune_result* out, void* stream) {
+  ED_GUARD_BEGIN
+  if (!h || !out) ED_INVALID("NULL argument");
+  ED_TRY_CUDA(cudaSetDevice(h->s.ctx->device));
+  return autotune(&h->s, reps, out, as_stream(stream));
+  ED_GUARD_END
+}
+
+int ed_sector_set_variant(ed_sector* h, int variant) {
+  ED_GUARD_BEGIN
+  if (!h) ED_INVALID("NULL argument");
+  if (variant != -1 && !fast_variant_applies(&h->s, variant))
+    ED_INVALID("H*v variant %d does not apply to this sector", variant);
+  h->s.tune = variant;
+  return ED_OK;
+  ED_GUARD_END
+}
+
+int ed_sector_get_variant(const ed_sector* h, int* variant) {
+  ED_GUARD_BEGIN
+  if (!h || !variant) ED_INVALID("NULL argument");
+  *variant = fast_variant_applies(&h->s, h->s.tune) ? h->s.tune : -1;
+  return ED_OK;
+  ED_GUARD_END
+}
+
+int ed_tune_cache_save(ed_ctx* ctx, const char* path) {
+  ED_GUARD_BEGIN
+  if (!ctx || !path) ED_INVALID("NULL argument");
+  return tune_cache_save(&ctx->c, path);
+  ED_GUARD_END
+}
+
+int ed_tune_cache_load(ed_ctx* ctx, const char* path, int* n_loaded) {
+  ED_GUARD_BEGIN
+  if (!ctx || !path) ED_INVALID("NULL argument");
+  int n = 0;
+  const int st = tune_cache_load(&ctx->c, path, &n);
+  if (n_loaded) *n_loaded = n;
+  return st;
   ED_GUARD_END
 }
 

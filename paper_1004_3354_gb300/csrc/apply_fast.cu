@@ -45,7 +45,7 @@ struct FastView {
   const uint32_t* row_pat;
   const uint4* perm4;           // [n_win*32] four entries per lane
   const uchar4* cnt4;           // [n_win] slot counts
-  const uint4* hop4;            // [n_win][max_cnt][32]
+  const uint4* hop4;            // [n_win][max_cnt][32] (single-row or two-row encoding, per kernel)
   const double* coef;
   const float2* coef_df;
   int n_coef;
@@ -325,14 +325,15 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
 }
 
 // ---------------------------------------------------------------- two rows
-// Float vectors run two rows per block: rows A and B share every down hop
-// (same hop word, same coefficient, same staged offset), so the two rows are
-// staged interleaved ({A, B} per rank), the coefficients are kept as
-// {hi, hi, lo, lo}, and one f32x2 instruction advances both rows' double-float
-// accumulators.  Hop words, window permutation and coefficient loads are
-// shared by the two rows.  (Double-float rows would need 16 bytes per rank:
-// two blocks of that size leave the SM too little L1, and the single-row
-// kernel is faster for them.)
+// Two up strings per block: rows A and B share every down hop (same hop word,
+// same coefficient, same staged offset), so the two rows are staged
+// interleaved ({A, B} per rank for floats, {A.hi, B.hi, A.lo, B.lo} for
+// double-float), the coefficients are kept as {hi, hi, lo, lo}, and one f32x2
+// instruction advances both rows' double-float accumulators.  Hop words,
+// window permutation and coefficient loads are shared by the two rows.  It is
+// the default for float vectors; for double-float rows (16 bytes per rank) two
+// blocks leave the SM little L1 and the single-row kernel is usually faster,
+// which the autotuner measures per sector.
 __device__ __forceinline__ void cp_async4(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g));
@@ -340,6 +341,25 @@ __device__ __forceinline__ void cp_async4(void* s, const void* g) {
 
 template <class P>
 struct PairTraits;
+
+template <>
+struct PairTraits<PolDF> {
+  using PV = float4;  // {A.hi, B.hi, A.lo, B.lo}
+  static constexpr bool XLO = true;
+  __device__ static __forceinline__ float2 hi(const PV& v) { return make_float2(v.x, v.y); }
+  __device__ static __forceinline__ float2 lo(const PV& v) { return make_float2(v.z, v.w); }
+  __device__ static __forceinline__ float2 hi2(float2 a, float2 b) { return make_float2(a.x, b.x); }
+  __device__ static __forceinline__ float2 lo2(float2 a, float2 b) { return make_float2(a.y, b.y); }
+  __device__ static __forceinline__ void stage(PV* s, const float2* a, const float2* b) {
+    cp_async4(&s->x, &a->x);
+    cp_async4(&s->y, &b->x);
+    cp_async4(&s->z, &a->y);
+    cp_async4(&s->w, &b->y);
+  }
+  __device__ static __forceinline__ float2 out(float h, float l) { return df_norm(make_float2(h, l)); }
+  __device__ static __forceinline__ float2 xa(const PV& v) { return make_float2(v.x, v.z); }
+  __device__ static __forceinline__ float2 xb(const PV& v) { return make_float2(v.y, v.w); }
+};
 
 template <>
 struct PairTraits<PolF32> {
@@ -755,7 +775,9 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double
 
 template <class P, int BS, int MINB>
 int launch_pair(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+  if (!s->fast.pair_ok) ED_INVALID("the sector has no two-row kernel tables");
   FastView F = make_view<P>(s);
+  F.hop4 = reinterpret_cast<const uint4*>(s->fast.hop2);
   F.dotp = dotp;
   size_t smem = pair_smem<P>(F.D, F.n_coef);
   auto kern = k_apply_pair<P, BS, MINB>;
@@ -770,17 +792,30 @@ int launch_pair(const Sector* s, const void* x, void* y, cudaStream_t st, double
   return ED_OK;
 }
 
-// FP64 and double-float: three 256-thread single-row blocks per SM (shared
-// memory and registers both bound it).  Float rows: two-row blocks, three per SM.
+// H*v variants of the fast path: up strings per block (one: k_apply_win, two:
+// k_apply_pair) times a launch shape (threads per block, the blocks per SM the
+// register budget is sized for; shared memory may allow fewer).
+constexpr int kNShapes = 4;
+constexpr int kShapeBS[kNShapes] = {256, 192, 256, 512};
+constexpr int kShapeMinB[kNShapes] = {3, 4, 2, 1};
+
 template <class P>
-int dispatch(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
-  if constexpr (P::prec != ED_PREC_FP32) {
-    if (s->fast.pair) ED_INVALID("row kernel tables were built for another vector format");
-    return launch_fast<P, 256, 3>(s, x, y, st, dotp, nparts);
-  } else {
-    if (!s->fast.pair) ED_INVALID("row kernel tables were built for another vector format");
-    return launch_pair<P, 256, 3>(s, x, y, st, dotp, nparts);
+int run_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+  switch (v) {
+    case 0: return launch_fast<P, 256, 3>(s, x, y, st, dotp, nparts);
+    case 1: return launch_fast<P, 192, 4>(s, x, y, st, dotp, nparts);
+    case 2: return launch_fast<P, 256, 2>(s, x, y, st, dotp, nparts);
+    case 3: return launch_fast<P, 512, 1>(s, x, y, st, dotp, nparts);
   }
+  if constexpr (P::prec != ED_PREC_FP64) {
+    switch (v) {
+      case 4: return launch_pair<P, 256, 3>(s, x, y, st, dotp, nparts);
+      case 5: return launch_pair<P, 192, 4>(s, x, y, st, dotp, nparts);
+      case 6: return launch_pair<P, 256, 2>(s, x, y, st, dotp, nparts);
+      case 7: return launch_pair<P, 512, 1>(s, x, y, st, dotp, nparts);
+    }
+  }
+  ED_INVALID("H*v variant %d does not apply to this sector", v);
 }
 
 }  // namespace
@@ -814,14 +849,15 @@ int build_fast(Sector* s) {
     zero_id = (int)coef.size();
     coef.push_back(0.0);
   }
-  // float rows run the two-row kernel, the other formats the single-row one;
-  // hop words address the staged row in bytes below 2^19
-  const bool pair = s->prec == ED_PREC_FP32;
-  const size_t vbytes = (pair ? 2 : 1) * elem_bytes(s->prec);
+  // single-row tables always; two-row tables (double-float and float rows)
+  // where two interleaved rows fit.  Hop words address the staged row in
+  // bytes below 2^19.
+  const size_t vbytes = elem_bytes(s->prec);
   if ((uint64_t)D * vbytes >= (1ull << 19)) return ED_OK;
   const int nc = (int)coef.size();
-  const size_t smem = pair ? pair_smem<PolF32>(D, nc) : std::max(fast_smem<PolF64>(D, nc), fast_smem<PolDF>(D, nc));
-  if (smem > 220 * 1024) return ED_OK;
+  if (std::max(fast_smem<PolF64>(D, nc), fast_smem<PolDF>(D, nc)) > 220 * 1024) return ED_OK;
+  const size_t smem2 = s->prec == ED_PREC_DF64 ? pair_smem<PolDF>(D, nc) : pair_smem<PolF32>(D, nc);
+  const bool pair = s->prec != ED_PREC_FP64 && (uint64_t)D * 2 * vbytes < (1ull << 19) && smem2 <= 220 * 1024;
   const bool mix_delta = s->dn_move && s->orb0 + s->M == s->n_s && s->M * s->M * (1 << s->M) <= kMaxDelta;
 
   // window-local order: inside each window of 128 ranks, longest hop list first
@@ -868,7 +904,7 @@ int build_fast(Sector* s) {
     rkey[u] = cmask.size() <= 12 ? k : 0;
   }
   std::iota(rorder.begin(), rorder.end(), 0u);
-  if (pair) {
+  {
     // inside a component, rows with equal up-hop and mixed-list lengths sit
     // next to each other, so the two rows of a pair pad their lists little
     std::vector<uint32_t> uptr(Du + 1), mptr;
@@ -884,8 +920,6 @@ int build_fast(Sector* s) {
       if (rkey[a] != rkey[b]) return rkey[a] < rkey[b];
       return lens(a) < lens(b);
     });
-  } else {
-    std::stable_sort(rorder.begin(), rorder.end(), [&](uint32_t a, uint32_t b) { return rkey[a] < rkey[b]; });
   }
 
   auto& f = s->fast;
@@ -907,7 +941,7 @@ int build_fast(Sector* s) {
   ED_TRY_CUDA(cudaMemcpy(f.coef, coef.data(), sizeof(double) * f.n_coef, cudaMemcpyHostToDevice));
   ED_TRY_CUDA(cudaMemcpy(f.row_order, rorder.data(), sizeof(uint32_t) * Du, cudaMemcpyHostToDevice));
   f.mix_delta = mix_delta;
-  f.pair = pair;
+  f.pair_ok = pair;
   if (mix_delta) {
     const int M = s->M, NP = 1 << M;
     std::vector<uint32_t> dbas(D), wpat(n_win, 0xffffffffu);
@@ -927,9 +961,16 @@ int build_fast(Sector* s) {
   }
   k_win_tables<<<(unsigned)((NE + 127) / 128), 128>>>(D, n_win, f.max_cnt, f.perm, s->dn.basis, s->dn.hop_ptr,
                                                       s->dn.hop_tgt, s->dn.hop_val, f.coef, f.n_coef, zero_id,
-                                                      (int)vbytes, pair ? 16 : 8,
+                                                      (int)vbytes, 8,
                                                       f.hop, s->dn.e, (s->n_chunks == 1) ? s->W : nullptr, s->w_lo,
                                                       wbits, f.n_pat, f.dd, s->orb0, f.dpat);
+  if (pair) {
+    ED_TRY(sector_alloc(s, &f.hop2, (size_t)f.max_cnt * NE));
+    k_win_tables<<<(unsigned)((NE + 127) / 128), 128>>>(D, n_win, f.max_cnt, f.perm, s->dn.basis, s->dn.hop_ptr,
+                                                        s->dn.hop_tgt, s->dn.hop_val, f.coef, f.n_coef, zero_id,
+                                                        (int)(2 * vbytes), 16, f.hop2, s->dn.e, nullptr, s->w_lo,
+                                                        wbits, 0, nullptr, s->orb0, nullptr);
+  }
   ED_LAUNCH_CHECK();
   k_row_pat<<<(Du + 127) / 128, 128>>>(Du, s->up.basis, s->w_lo, wbits, f.row_pat);
   ED_LAUNCH_CHECK();
@@ -945,13 +986,38 @@ int build_fast(Sector* s) {
   return ED_OK;
 }
 
-int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+int fast_variants() { return 2 * kNShapes; }
+
+void fast_variant_info(int v, int* kernel, int* block, int* min_blocks) {
+  *kernel = v < kNShapes ? 2 : 3;
+  *block = kShapeBS[v % kNShapes];
+  *min_blocks = kShapeMinB[v % kNShapes];
+}
+
+bool fast_variant_applies(const Sector* s, int v) {
+  if (!s->fast.ok || v < 0 || v >= 2 * kNShapes) return false;
+  return v < kNShapes || s->fast.pair_ok;
+}
+
+// Untuned choice: two rows per block for float vectors, one otherwise.
+int fast_default_variant(const Sector* s) {
+  return (s->prec == ED_PREC_FP32 && s->fast.pair_ok) ? kNShapes : 0;
+}
+
+int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp,
+                       int* nparts) {
+  if (!fast_variant_applies(s, v)) ED_INVALID("H*v variant %d does not apply to this sector", v);
   switch (s->prec) {
-    case ED_PREC_FP64: return dispatch<PolF64>(s, x, y, st, dotp, nparts);
-    case ED_PREC_DF64: return dispatch<PolDF>(s, x, y, st, dotp, nparts);
-    case ED_PREC_FP32: return dispatch<PolF32>(s, x, y, st, dotp, nparts);
+    case ED_PREC_FP64: return run_variant<PolF64>(s, v, x, y, st, dotp, nparts);
+    case ED_PREC_DF64: return run_variant<PolDF>(s, v, x, y, st, dotp, nparts);
+    case ED_PREC_FP32: return run_variant<PolF32>(s, v, x, y, st, dotp, nparts);
   }
   ED_INVALID("unknown precision");
+}
+
+int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
+  const int v = fast_variant_applies(s, s->tune) ? s->tune : fast_default_variant(s);
+  return apply_fast_variant(s, v, x, y, st, dotp, nparts);
 }
 
 }  // namespace ed

@@ -6,6 +6,8 @@
 
 #include <atomic>
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -45,6 +47,9 @@ void set_error(const char* fmt, ...);
 // ------------------------------------------------------------------ context
 struct Ctx {
   int device = 0;
+  std::string device_name;       // cudaDeviceProp::name, keys the autotune cache
+  std::mutex tune_mu;
+  std::map<std::string, int> tune_cache;  // sector shape key -> fast H*v variant
   size_t budget = 0;      // 0 = unlimited
   std::atomic<size_t> in_use{0};
   int num_sms = 0;
@@ -161,12 +166,15 @@ struct Sector {
     uint8_t* dpat = nullptr;        // [n_win*128] impurity pattern of each entry
     uint32_t* wpat = nullptr;       // [n_win] pattern shared by a whole window, or ~0u
     int32_t* mdelta = nullptr;      // [M*M][2^M] (shift << 1 | sign) or INT32_MIN
-    // two-row kernel (float vectors): rows are processed in pairs
-    // (row_order[2i], row_order[2i+1]) staged interleaved, and the hop words
+    // two-row kernel (double-float and float vectors): rows are processed in
+    // pairs (row_order[2i], row_order[2i+1]) staged interleaved; its hop words
     // hold byte offsets into that interleaved row and into a table of 16-byte
     // coefficient entries
-    bool pair = false;
+    bool pair_ok = false;
+    uint32_t* hop2 = nullptr;   // [n_win][max_cnt][32][4] two-row encoding
   } fast;
+  // autotuned H*v variant of the fast path (apply_fast.cu), -1 = untuned
+  int tune = -1;
   // stored CSR (optional)
   uint64_t csr_nnz = 0;
   uint64_t* csr_ptr = nullptr;
@@ -202,6 +210,18 @@ int build_fast(Sector* s);
 // to dotp[0 .. *nparts).
 int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp = nullptr,
                int* nparts = nullptr);
+// Autotune cache key of a sector's shape (tune.cu); the cached variant is
+// applied when a sector with that key is created.
+std::string tune_key(const Sector* s);
+void tune_apply_cached(Sector* s);
+
+// Variants of the fast H*v path (apply_fast.cu): index v in [0, fast_variants()).
+int fast_variants();
+void fast_variant_info(int v, int* kernel, int* block, int* min_blocks);
+bool fast_variant_applies(const Sector* s, int v);
+int fast_default_variant(const Sector* s);
+int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp = nullptr,
+                       int* nparts = nullptr);
 
 // Apply entry points (apply.cu, csr.cu)
 int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st);
