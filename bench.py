@@ -49,7 +49,7 @@ def args_parse(argv=None):
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--no-autotune", action="store_true", help="time the untuned default H*v variant")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15", "lowest8"],
+    p.add_argument("--workload", default="hv15", choices=["hv15", "sectors12", "serve", "solve15", "lowest8", "dmft"],
                    help="hv15: H*v at N_s=15 (default); sectors12: 8 lowest states of all 169 sectors at N_s=12; "
                         "serve: Poisson stream of impurity solves, N_s in 10..16; "
                         "solve15: N_s=15 ground state + G(i w_n) per vector format, and the stored-CSR H*v")
@@ -597,6 +597,94 @@ def run_solve15(a):
     print(json.dumps(out), flush=True)
 
 
+def dmft_loop(ed, ctx, torch, n_s, U=2.0, t=0.5, beta=40.0, n_w=512, n_fit=64, n_iter=20, prec="df64",
+              tol=1e-10, conv=1e-5, n_k=256, neighbours=True, depth=150, log=None):
+    """ED/DMFT for the one-band Hubbard model on the square lattice at half
+    filling (Sec. 3.2: U = 2, t = 0.5): each iteration builds the AIM of the
+    current bath, finds the ground state of the half-filled sector (and of its
+    four neighbours, weighted by Boltzmann factors), forms G(i w_n) by
+    continued fractions and updates the bath with ed_dmft_update.  Stops when
+    G changes by less than `conv` on every frequency.  Every step runs in the
+    library; this function only passes data between its calls."""
+    import workloads as W
+    mu = U / 2.0
+    eps_d = -mu
+    e, w = W.square_lattice_energies(t, n_k)
+    eps, V = W.dmft_initial_bath(n_s - 1, half_width=2 * t, v=0.3)
+    half = n_s // 2
+    sectors = [(half, half)]
+    if neighbours:
+        sectors += [(half + 1, half), (half, half + 1), (half - 1, half), (half, half - 1)]
+    G_prev, hist = None, []
+    p = ed.PREC_NAMES[prec]
+    for it in range(n_iter):
+        t0 = time.perf_counter()
+        m = W.aim_bath(eps_d, U, eps, V)
+        states = []
+        for nu, nd in sectors:
+            sec = ed.ed_sector_create(ctx, m, nu, nd, prec)
+            dim = ed.ed_sector_get_info(sec).dim
+            psi = torch.empty(dim * ed.elems_per_value(p), dtype=ed.torch_dtype(p), device="cuda")
+            ev, info, st = ed.ed_lanczos(sec, k=1, tol=tol, max_iter=600, reorth=False, evecs=psi,
+                                         allow_not_converged=True)
+            states.append((nu, nd, float(ev[0]), psi))
+            ed.ed_sector_destroy(sec)
+        t1 = time.perf_counter()
+        G = ed.ed_greens_cf(ctx, m, prec, states, beta, n_w, orbital=m.orb0, spin=0, depth=depth)
+        t2 = time.perf_counter()
+        eps, V, c2, sig, gl, dn = ed.ed_dmft_update(ctx, G, beta, eps_d, mu, eps, V, e, w, n_fit)
+        t3 = time.perf_counter()
+        dG = None if G_prev is None else float(np.max(np.abs(G - G_prev)))
+        E = [s_[2] for s_ in states]
+        rec = {"iter": it, "dG": dG, "chi2": c2, "E0": min(E), "ground_sector": list(sectors[int(np.argmin(E))]),
+               "solve_s": t1 - t0, "greens_s": t2 - t1, "update_s": t3 - t2, "total_s": t3 - t0}
+        hist.append(rec)
+        if log:
+            log(rec)
+        G_prev = G
+        del states
+        if dG is not None and dG < conv:
+            break
+    wn = np.pi / beta
+    Z = 1.0 / (1.0 - sig[0].imag / wn)  # quasiparticle weight estimate from the lowest Matsubara point
+    return {"history": hist, "G": G, "Sigma": sig, "G_loc": gl, "eps": eps, "V": V, "Z": Z,
+            "converged": bool(hist[-1]["dG"] is not None and hist[-1]["dG"] < conv)}
+
+
+def run_dmft(a):
+    """ED/DMFT of the one-band Hubbard model on the square lattice at half
+    filling, U = 2, t = 0.5 (Sec. 3.2), beta = 40: the N_s = 8 loop to
+    self-consistency, and the time of one ED/DMFT iteration at N_s = 16 (the
+    unit of the paper's Table 1, there 382-602 s on 256-512 CPU cores)."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    ctx = ed.ed_ctx_create(0)
+    out = {"metric": "ED/DMFT: iterations to self-consistency (N_s=8) and seconds per iteration (N_s=16)",
+           "n_gpus": 1, "data": "square-lattice Hubbard model, U=2, t=0.5, beta=40, half filling",
+           "vector_format": "df64", "results": {}}
+    r8 = dmft_loop(ed, ctx, torch, 8, n_iter=40)
+    out["results"]["ns8_loop"] = {
+        "iterations": len(r8["history"]), "converged": r8["converged"], "final_dG": r8["history"][-1]["dG"],
+        "final_chi2": r8["history"][-1]["chi2"], "Z": r8["Z"], "seconds_per_iteration":
+            float(np.mean([h["total_s"] for h in r8["history"]])),
+        "max_abs_re_G": float(np.max(np.abs(r8["G"].real))), "bath_eps": r8["eps"].tolist(),
+        "bath_V": r8["V"].tolist()}
+    r16 = dmft_loop(ed, ctx, torch, 16, n_iter=2)
+    h = r16["history"]
+    out["results"]["ns16_iteration"] = {
+        "iterations_run": len(h), "seconds": [x["total_s"] for x in h],
+        "solve_s": [x["solve_s"] for x in h], "greens_s": [x["greens_s"] for x in h],
+        "update_s": [x["update_s"] for x in h], "E0": [x["E0"] for x in h],
+        "sectors": "(8,8) and its four neighbours, ground state each",
+        "paper_context": "Table 1: one iteration at N_s=16 took 602 s on 256 and 382 s on 512 CPU cores"}
+    ed.ed_ctx_destroy(ctx)
+    print(json.dumps(out), flush=True)
+
+
 def run_lowest8(a):
     """Eight lowest states (k = 8, DF64 vectors, tol 1e-10): the N_s=15 (7,8)
     sector by Lanczos with a full CGS2 basis and by thick-restart Lanczos with a
@@ -657,5 +745,7 @@ if __name__ == "__main__":
         run_solve15(a)
     elif a.workload == "lowest8":
         run_lowest8(a)
+    elif a.workload == "dmft":
+        run_dmft(a)
     else:
         run_ours(a)

@@ -329,6 +329,30 @@ int ed_greens_cf_z(ed_ctx* ctx, const ed_model* model, int prec, int n_states,
                    const ed_state* states, double beta, int n_z, const double* z, int orbital,
                    int spin, int depth, double boltz_cut, double* G, double* coeffs, void* stream);
 
+/* ------------------------------------------------- DMFT self-consistency */
+/* One DMFT self-consistency update for the one-band Hubbard model (Sec. 2: the
+ * lattice problem is mapped onto the Anderson impurity of Eq. 2; Sec. 3.2 runs
+ * it on the square lattice).  Inputs (host): the impurity G(i w_n), n < n_w,
+ * w_n = (2n+1) pi / beta (2*n_w doubles, re/im interleaved; e.g. from
+ * ed_greens_cf) of the AIM with impurity level eps_d and bath eps_in, V_in
+ * (n_bath each); the chemical potential mu; a quadrature of the lattice band,
+ * energies e and weights w (n_e each, weights summing to 1).  Computes on the
+ * device, at z = i w_n,
+ *   Delta     = sum_k V_k^2 / (z - eps_k),
+ *   Sigma     = z - eps_d - Delta - 1 / G_imp,
+ *   G_loc     = sum_j w_j / (z + mu - e_j - Sigma),
+ *   Delta_new = z - eps_d - Sigma - 1 / G_loc,
+ * and fits the new bath eps_out, V_out (V >= 0) to Delta_new on the first n_fit
+ * frequencies by Levenberg-Marquardt started from eps_in, V_in, minimising
+ * chi2 = (1/n_fit) sum_n |Delta_new - sum_k V_k^2 / (z - eps_k)|^2.  Optional
+ * outputs (host, 2*n_w doubles each, NULL to skip): Sigma, G_loc, Delta_new.
+ * ED_ERR_INVALID for sizes out of range (1 <= n_bath <= ED_MAX_SITES,
+ * 1 <= n_fit <= n_w, n_e >= 1) or a zero or non-finite G_imp.  Synchronises. */
+int ed_dmft_update(ed_ctx* ctx, int n_w, double beta, const double* G_imp, double eps_d, double mu,
+                   int n_bath, const double* eps_in, const double* V_in, int n_e, const double* e,
+                   const double* w, int n_fit, double* eps_out, double* V_out, double* chi2,
+                   double* sigma, double* G_loc, double* delta_new, void* stream);
+
 /* ------------------------------------------------------- batched sectors */
 typedef struct ed_batch ed_batch;
 

@@ -132,6 +132,10 @@ _SIGS = {
     "ed_dot_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double), C.c_void_p]),
     "ed_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                              C.POINTER(ed_lanczos_info), C.c_void_p]),
+    "ed_dmft_update": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                 C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                 C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
     "ed_sector_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ed_tune_result), C.c_void_p]),
     "ed_sector_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "ed_sector_get_variant": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
@@ -317,6 +321,27 @@ def ed_lanczos(sec, k=1, tol=1e-12, max_iter=300, check_every=10, seed=1, v0=Non
                           _stream(stream))
     check(st, allow=(ED_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return ev, info, st
+
+
+def ed_dmft_update(ctx, G_imp, beta, eps_d, mu, eps, V, e, w, n_fit, stream=None):
+    """One DMFT self-consistency update.  G_imp: complex ndarray[n_w] at
+    w_n = (2n+1) pi / beta; e, w: band-energy quadrature.  Returns
+    (eps_new, V_new, chi2, Sigma, G_loc, Delta_new) with complex ndarrays."""
+    def f64(a):
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    g = np.ascontiguousarray(np.asarray(G_imp, dtype=np.complex128)).view(np.float64)
+    n_w = g.size // 2
+    eps, V, e, w = f64(eps), f64(V), f64(e), f64(w)
+    nb = eps.size
+    eo, vo = np.zeros(nb), np.zeros(nb)
+    outs = [np.zeros(2 * n_w) for _ in range(3)]
+    c2 = C.c_double(0.0)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    check(lib().ed_dmft_update(ctx, n_w, float(beta), vp(g), float(eps_d), float(mu), nb, vp(eps), vp(V),
+                               e.size, vp(e), vp(w), int(n_fit), vp(eo), vp(vo), C.byref(c2),
+                               vp(outs[0]), vp(outs[1]), vp(outs[2]), _stream(stream)))
+    cx = [o[0::2] + 1j * o[1::2] for o in outs]
+    return eo, vo, c2.value, cx[0], cx[1], cx[2]
 
 
 def ed_sector_autotune(sec, reps=5, stream=None):

@@ -68,6 +68,10 @@ int lanczos_run(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs,
 int trlan_run(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed_trlan_info* info,
               cudaStream_t st);
 int autotune(Sector* s, int reps, ed_tune_result* out, cudaStream_t st);
+int dmft_update(Ctx* ctx, int n_w, double beta, const double* G_imp, double eps_d, double mu, int n_bath,
+                const double* eps_in, const double* V_in, int n_e, const double* e, const double* w, int n_fit,
+                double* eps_out, double* V_out, double* chi2, double* sigma, double* G_loc, double* delta_new,
+                cudaStream_t st);
 int tune_cache_save(Ctx* c, const char* path);
 int tune_cache_load(Ctx* c, const char* path, int* n_loaded);
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
@@ -357,6 +361,18 @@ int ed_lanczos(ed_sector* h, const ed_lanczos_opts* opts, double* evals, void* e
   if (info) std::memset(info, 0, sizeof(*info));
   ED_TRY_CUDA(cudaSetDevice(h->s.ctx->device));
   return lanczos_run(&h->s, opts, evals, evecs, info, as_stream(stream));
+  ED_GUARD_END
+}
+
+int ed_dmft_update(ed_ctx* ctx, int n_w, double beta, const double* G_imp, double eps_d, double mu, int n_bath,
+                   const double* eps_in, const double* V_in, int n_e, const double* e, const double* w, int n_fit,
+                   double* eps_out, double* V_out, double* chi2, double* sigma, double* G_loc, double* delta_new,
+                   void* stream) {
+  ED_GUARD_BEGIN
+  if (!ctx) ED_INVALID("NULL argument");
+  ED_TRY_CUDA(cudaSetDevice(ctx->c.device));
+  return dmft_update(&ctx->c, n_w, beta, G_imp, eps_d, mu, n_bath, eps_in, V_in, n_e, e, w, n_fit, eps_out, V_out,
+                     chi2, sigma, G_loc, delta_new, as_stream(stream));
   ED_GUARD_END
 }
 

@@ -52,9 +52,11 @@ struct Rec3 {
   int init() {  // q_0 already in Q[0]
     return dot_to(*W, (const V*)q(0), (const V*)q(0), OP_SIGMA0, 0);
   }
-  int step(int j, double thr) {
+  int step(int j, double thr, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     int np = 0;
+    if (e0) ED_TRY_CUDA(cudaEventRecord(e0, W->st));
     ED_TRY(apply_dot(q(j), Y, &np));
+    if (e1) ED_TRY_CUDA(cudaEventRecord(e1, W->st));
     k_finish<<<1, kRedThreads, 0, W->st>>>(W->partial, np, OP_ALPHA_Q, j, W->c, 0.0);
     k_lz_step<V><<<sgrid, kRedThreads, 0, W->st>>>(Y, q(j), j > 0 ? q(j - 1) : nullptr, q(j + 1), W->n, W->c, j,
                                                    W->partial);
@@ -169,8 +171,19 @@ int lanczos3_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evec
   std::vector<double> h_theta(ED_MAX_K), h_res(ED_MAX_K);
   int m = 0, n_conv = 0, status = ED_OK;
   const double thr = 1e-13;
+  // one event pair per step times the H*v launches of the recurrence
+  std::vector<cudaEvent_t> evs(2 * (size_t)mmax);
+  for (auto& e : evs) ED_TRY_CUDA(cudaEventCreate(&e));
+  struct EvGuard {
+    std::vector<cudaEvent_t>* v;
+    ~EvGuard() {
+      for (auto e : *v) cudaEventDestroy(e);
+    }
+  } evguard{&evs};
+  int n_steps = 0;
   for (int j = 0; j < mmax; ++j) {
-    ED_TRY(R.step(j, thr));
+    ED_TRY(R.step(j, thr, evs[2 * j], evs[2 * j + 1]));
+    n_steps = j + 1;
     m = j + 1;
     bool check = ((m % check_every) == 0) || (m == mmax) || (n <= 4096);
     if (!check) continue;
@@ -222,9 +235,16 @@ int lanczos3_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evec
     ED_LAUNCH_CHECK();
   }
   ED_TRY_CUDA(cudaStreamSynchronize(st));
-  if (info)
+  if (info) {
+    double apply_ms = 0.0;
+    for (int q = 0; q < n_steps; ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, evs[2 * q], evs[2 * q + 1]) == cudaSuccess) apply_ms += ms;
+    }
+    info->apply_ms = apply_ms;
     info->total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  }
   if (status != ED_OK) set_error("Lanczos did not converge in %d steps", mmax);
   return status;
 }

@@ -134,6 +134,7 @@ def test_without_reorthogonalisation_ground_state(env):
         v = torch.empty(n, dtype=torch.float64, device="cuda")
         ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-11, max_iter=300, reorth=False, evecs=v)
         assert ev_err(ev, ref) <= 1e-10
+        assert 0.0 < info.apply_ms < info.total_ms
         vv = v.cpu().numpy()
         assert abs(abs(vv @ refv[:, 0]) - 1.0) <= 1e-9
     finally:

@@ -97,6 +97,49 @@ def check_cf_vs_lehmann_real_axis():
     assert np.max(np.abs(Gcf - Gl)) < 1e-10, np.max(np.abs(Gcf - Gl))
 
 
+def check_dmft_atomic_self_energy():
+    """Hubbard atom at half filling (V = 0, eps_d = -U/2): Sigma(i w) = U/2 + U^2 / (4 i w)."""
+    from oracle import dmft
+    U, beta = 2.0, 20.0
+    m = W.aim_bath(-U / 2, U, [0.0], [0.0])
+    G = greens.lehmann(m, beta, 64, orbital=m.orb0, spin=fock.UP)
+    iw = 1j * greens.matsubara(beta, 64)
+    sig = dmft.self_energy(iw, G, -U / 2, [0.0], [0.0])
+    ref = U / 2 + U * U / (4 * iw)
+    assert np.max(np.abs(sig - ref)) < 1e-12, np.max(np.abs(sig - ref))
+
+
+def check_dmft_noninteracting():
+    """U = 0: the impurity self-energy vanishes for any bath, and the square-lattice
+    local Green's function has the band's moments: i w G -> 1, (i w)^3 (G - 1/(i w)) -> 4 t^2."""
+    from oracle import dmft
+    t, beta = 0.5, 30.0
+    eps, V = np.array([-0.7, 0.1, 0.9]), np.array([0.3, 0.25, 0.4])
+    m = W.aim_bath(0.0, 0.0, eps, V)
+    G = greens.lehmann(m, beta, 40, orbital=m.orb0, spin=fock.UP)
+    iw = 1j * greens.matsubara(beta, 40)
+    assert np.max(np.abs(dmft.self_energy(iw, G, 0.0, eps, V))) < 1e-12
+    e, w = W.square_lattice_energies(t, 128)
+    assert abs(w.sum() - 1.0) < 1e-14 and abs((w * e).sum()) < 1e-14 and abs((w * e * e).sum() - 4 * t * t) < 1e-13
+    z = 1j * np.array([200.0, 400.0])
+    gl = dmft.lattice_gloc(z, np.zeros(2), 0.0, e, w)
+    # z G = 1 + m1 / z + m2 / z^2 + ..., m1 = 0, m2 = 4 t^2
+    assert np.max(np.abs(z * gl - 1.0 - 4 * t * t / z ** 2)) < 1e-8
+    assert abs(((z ** 3) * (gl - 1.0 / z))[-1].real - 4 * t * t) < 1e-3
+
+
+def check_dmft_bath_fit_recovers_bath():
+    """A hybridisation made from a known bath is fitted back (chi2 ~ 0) from a perturbed start."""
+    from oracle import dmft
+    iw = 1j * greens.matsubara(40.0, 64)
+    eps, V = np.array([-1.1, -0.3, 0.4, 1.2]), np.array([0.35, 0.2, 0.25, 0.4])
+    target = dmft.hybridisation(iw, eps, V)
+    e2, v2, c2 = dmft.fit_bath(iw, target, eps + 0.07 * np.array([1, -1, 1, -1]), V * 1.1)
+    assert c2 < 1e-20, c2
+    o = np.argsort(e2)
+    assert np.max(np.abs(e2[o] - eps)) < 1e-6 and np.max(np.abs(v2[o] - V)) < 1e-6
+
+
 def multiset(vals, tol=1e-9):
     vals = np.sort(np.asarray(vals))
     out = []
@@ -270,6 +313,7 @@ PINS = [check_two_site_hubbard, check_u0_ground_energy, check_u0_greens, check_t
         check_hermitian, check_conservation_and_blocks, check_particle_hole, check_spin_symmetry,
         check_su2_inclusion, check_cf_vs_lehmann, check_sum_rules, check_fig1_csr,
         check_u0_greens_real_axis, check_spectral_sum_rule, check_cf_vs_lehmann_real_axis,
+        check_dmft_atomic_self_energy, check_dmft_noninteracting, check_dmft_bath_fit_recovers_bath,
         check_sector_dims, check_tiers_agree, check_row_sampling]
 
 

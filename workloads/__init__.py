@@ -111,6 +111,47 @@ def aim(n_s: int = 6, seed: int = 0, U: float = 4.0, eps_d: float = 0.0, mu: flo
                              eps_range=list(eps_range), v_range=list(v_range)))
 
 
+def aim_bath(eps_d: float, U: float, eps, V, imp_first: bool = False) -> Model:
+    """Single-orbital Anderson impurity (Eq. 2) with the given bath levels eps_k
+    and hybridisations V_k (a DMFT iteration's bath); eps_d is the impurity
+    level including any chemical potential."""
+    eps = np.asarray(eps, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    nb = len(eps)
+    n_s = nb + 1
+    imp, bath = _sites(n_s, 1, imp_first)
+    d = imp[0]
+    T = np.zeros((n_s, n_s))
+    T[d, d] = eps_d
+    for k in range(nb):
+        s = bath[k]
+        T[s, s] = eps[k]
+        T[d, s] = T[s, d] = V[k]
+    Us = np.zeros(n_s)
+    Us[d] = U
+    return Model(n_s, T, Us, n_orb=1, name=f"aim_bath{n_s}", orb0=d,
+                 params=dict(kind="aim_bath", U=U, eps_d=eps_d, eps=eps.tolist(), V=V.tolist(),
+                             imp_first=imp_first))
+
+
+def square_lattice_energies(t: float = 0.5, n_k: int = 256):
+    """Band energies e(k) = -2t (cos kx + cos ky) of the square lattice with
+    nearest-neighbour hopping t (the Sec. 3.2 test model) on an n_k x n_k grid
+    of the Brillouin zone, as distinct values with their weights (summing to 1)."""
+    k = 2.0 * np.pi * (np.arange(n_k) + 0.5) / n_k
+    c = np.cos(k)
+    e = (-2.0 * t * (c[:, None] + c[None, :])).ravel()
+    e = np.round(e, 14)
+    vals, counts = np.unique(e, return_counts=True)
+    return vals, counts / float(n_k * n_k)
+
+
+def dmft_initial_bath(n_bath: int, half_width: float = 1.0, v: float = 0.3):
+    """Starting bath of a DMFT loop: levels spread evenly over [-w, w], equal V."""
+    eps = np.linspace(-half_width, half_width, n_bath) if n_bath > 1 else np.zeros(1)
+    return eps, np.full(n_bath, v)
+
+
 def kanamori_half_filling_mu(U: float, Up: float, J: float, n_orb: int) -> float:
     """mu placing the isolated Kanamori atom (eps_m = 0) at its particle-hole point."""
     return (U + (n_orb - 1) * (2.0 * Up - J)) / 2.0
