@@ -412,6 +412,11 @@ def run_sectors12(a):
     for prec in ("fp64", "fp32", "df64"):
         b = ed.ed_batch_create(ctx, model, secs, prec)
         tol = 1e-10 if prec != "fp32" else 1e-6
+        tune = None
+        if not a.no_autotune:
+            r = ed.ed_batch_autotune(b, steps=16)
+            tune = {"chosen_chunk": r.chunk[r.chosen], "ms_per_step": {
+                str(r.chunk[i]): round(r.ms_per_step[i], 4) for i in range(r.n_candidates)}}
         ed.ed_batch_lanczos(b, len(secs), k=8, tol=tol, max_iter=300, allow_not_converged=True)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -421,7 +426,7 @@ def run_sectors12(a):
         ed.ed_batch_destroy(b)
         out["results"][f"batched_{prec}"] = {"seconds": el, "solves_per_s": len(secs) / el, "steps": info.steps,
                                              "graph_replays": info.graph_replays,
-                                             "ground_energy_66": float(ev[6 * 13 + 6, 0])}
+                                             "ground_energy_66": float(ev[6 * 13 + 6, 0]), "packing": tune}
     # one sector at a time, FP64, no batching or graphs
     t0 = time.perf_counter()
     e66 = None

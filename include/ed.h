@@ -381,6 +381,23 @@ int ed_batch_destroy(ed_batch* b);
 int ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, double* evals, int* iters,
                      ed_batch_info* info, void* stream);
 
+/* Sector packing of the batch: every sector is cut into work items of `chunk`
+ * consecutive elements (1024 by default), and each batched kernel runs one
+ * launch over the item list.  ed_batch_set_chunk sets it (a power of two in
+ * 64..65536; ED_ERR_INVALID otherwise).  ed_batch_autotune runs `steps`
+ * graph-replayed Lanczos steps (2..64) of every sector with each candidate
+ * chunk (256 .. 32768), keeps the fastest per step and reports all of them;
+ * results do not depend on the chunk beyond the order of floating-point sums.
+ * Synchronises. */
+typedef struct ed_batch_tune_result {
+  int n_candidates;
+  int chosen;                       /* index of the chunk now in use */
+  int chunk[ED_MAX_TUNE];
+  double ms_per_step[ED_MAX_TUNE];  /* wall time per Lanczos step of the whole batch */
+} ed_batch_tune_result;
+int ed_batch_set_chunk(ed_batch* b, int chunk);
+int ed_batch_autotune(ed_batch* b, int steps, ed_batch_tune_result* out, void* stream);
+
 /* ---------------------------------------------------------------- serving */
 /* A request server for impurity solves, the work of one DMFT iteration (Sec. 2:
  * each iteration diagonalises a new impurity Hamiltonian and forms G(i w_n) of

@@ -80,6 +80,11 @@ class ed_tune_result(C.Structure):
                 ("ms", C.c_double * ED_MAX_TUNE)]
 
 
+class ed_batch_tune_result(C.Structure):
+    _fields_ = [("n_candidates", C.c_int), ("chosen", C.c_int), ("chunk", C.c_int * ED_MAX_TUNE),
+                ("ms_per_step", C.c_double * ED_MAX_TUNE)]
+
+
 class ed_batch_info(C.Structure):
     _fields_ = [("steps", C.c_int), ("graph_replays", C.c_int), ("n_sectors", C.c_int), ("total_ms", C.c_double)]
 
@@ -152,6 +157,8 @@ _SIGS = {
     "ed_batch_create": (C.c_int, [C.c_void_p, C.POINTER(ed_model), C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                   C.POINTER(C.c_void_p)]),
     "ed_batch_destroy": (C.c_int, [C.c_void_p]),
+    "ed_batch_set_chunk": (C.c_int, [C.c_void_p, C.c_int]),
+    "ed_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ed_batch_tune_result), C.c_void_p]),
     "ed_batch_lanczos": (C.c_int, [C.c_void_p, C.POINTER(ed_lanczos_opts), C.c_void_p, C.c_void_p,
                                    C.POINTER(ed_batch_info), C.c_void_p]),
     "ed_server_create": (C.c_int, [C.c_void_p, C.POINTER(ed_server_opts), C.POINTER(C.c_void_p)]),
@@ -454,6 +461,18 @@ def ed_batch_create(ctx, model, sectors, prec=ED_PREC_FP64):
 
 def ed_batch_destroy(b):
     return check(lib().ed_batch_destroy(b))
+
+
+def ed_batch_set_chunk(b, chunk):
+    check(lib().ed_batch_set_chunk(b, int(chunk)))
+
+
+def ed_batch_autotune(b, steps=16, stream=None):
+    """Time each sector-packing chunk on a few Lanczos steps; keeps the fastest.
+    Returns the ed_batch_tune_result."""
+    r = ed_batch_tune_result()
+    check(lib().ed_batch_autotune(b, int(steps), C.byref(r), _stream(stream)))
+    return r
 
 
 def ed_batch_lanczos(b, n_sectors, k=8, tol=1e-10, max_iter=300, check_every=10, seed=1, stream=None,

@@ -2,7 +2,8 @@
 // Lanczos step per replay of a single CUDA graph, and each kernel of the step
 // (one H*v over all sectors, the dot products, the update, CGS2 full
 // reorthogonalisation, the norm and the scaling) is ONE launch over a device
-// work list of (sector, 1024-element chunk) items.  The step index lives in
+// work list of (sector, chunk of consecutive elements) items (1024 elements by
+// default; ed_batch_autotune picks the chunk that packs the sectors fastest).  The step index lives in
 // device memory, so the graph captured once serves every step; sectors that
 // converge are switched off in a device flag array and their items return at
 // once.  This packs the many small sectors of a model (the 169 sectors of the
@@ -24,7 +25,7 @@ namespace ed {
 
 namespace {
 
-constexpr uint32_t kChunk = 1024;  // elements per work item
+constexpr uint32_t kChunkDefault = 1024;  // elements per work item unless tuned
 constexpr int kBT = 256;           // threads per block
 constexpr int kKB = 8;             // basis vectors per multi-dot register group
 
@@ -41,6 +42,7 @@ struct BatchDev {
   const JobDev* jobs;
   const uint2* items;  // {job, first element}
   uint32_t n_items;
+  uint32_t chunk;      // elements per item
   int n_jobs;
   uint64_t tot;        // elements per vector slot
   int* active;         // [n_jobs]
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(kBT) k_b_apply(BatchDev B, const typename P::V
     const V* x = Vb + (uint64_t)j * B.tot + J.off;
     V* y = w + J.off;
     const uint32_t Dd = J.S.D_dn;
-    const uint64_t e1 = min((uint64_t)item.y + kChunk, J.dim);
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
     for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) {
       const uint32_t u = (uint32_t)(e / Dd), d = (uint32_t)(e % Dd);
       const V* xr = x + (uint64_t)u * Dd;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(kBT) k_b_dot(BatchDev B, const V* __restrict__
     A acc{};
     if (B.active[item.x]) {
       const JobDev& J = B.jobs[item.x];
-      const uint64_t e1 = min((uint64_t)item.y + kChunk, J.dim);
+      const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
       const V* a = (mode == 0) ? Vb + (uint64_t)j * B.tot + J.off : w + J.off;
       const V* b = w + J.off;
       for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) bmac(acc, a[e], b[e]);
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kBT) k_b_multidot(BatchDev B, const V* __restr
     const uint2 item = B.items[it];
     const bool on = B.active[item.x] != 0;
     const JobDev& J = B.jobs[item.x];
-    const uint64_t e1 = min((uint64_t)item.y + kChunk, J.dim);
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
     for (int k0 = 0; k0 <= j; k0 += kKB) {
       A acc[kKB];
 #pragma unroll
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kBT) k_b_axpy(BatchDev B, V* __restrict__ Vb, 
     if (!B.active[item.x]) continue;
     const JobDev& J = B.jobs[item.x];
     const size_t base = (size_t)item.x * B.ms;
-    const uint64_t e1 = min((uint64_t)item.y + kChunk, J.dim);
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
     for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) {
       const uint64_t g = J.off + e;
       if (mode == 0) {
@@ -294,7 +296,7 @@ __global__ void k_b_random(BatchDev B, V* __restrict__ w, uint64_t seed) {
   for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
     const uint2 item = B.items[it];
     const JobDev& J = B.jobs[item.x];
-    const uint64_t e1 = min((uint64_t)item.y + kChunk, J.dim);
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
     for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) {
       const uint64_t r = bmix(seed * 0x2545f4914f6cdd1dull + (uint64_t)item.x * 0x9e3779b97f4a7c15ull + e);
       bset(w[J.off + e], (float)((r >> 40) * (1.0 / 16777216.0)) * 2.f - 1.f);
@@ -341,8 +343,10 @@ struct Batch {
   std::vector<JobDev> hjobs;
   std::vector<uint2> hitems;
   uint64_t tot = 0;
+  uint32_t chunk = kChunkDefault;
   JobDev* djobs = nullptr;
-  uint2* ditems = nullptr;
+  uint2* ditems = nullptr;   // owned separately: rebuilt when the chunk changes
+  size_t ditems_bytes = 0;
   std::vector<std::pair<void*, size_t>> allocs;
   cudaStream_t stream = nullptr;
   template <class T>
@@ -351,9 +355,32 @@ struct Batch {
     if (st == ED_OK) allocs.push_back({(void*)*p, std::max<size_t>(n, 1) * sizeof(T)});
     return st;
   }
+  // Cut every sector into items of `c` elements and upload the list.
+  int set_chunk(uint32_t c) {
+    hitems.clear();
+    for (size_t q = 0; q < hjobs.size(); ++q) {
+      hjobs[q].item0 = (uint32_t)hitems.size();
+      for (uint64_t e = 0; e < hjobs[q].dim; e += c) hitems.push_back(make_uint2((unsigned)q, (unsigned)e));
+      hjobs[q].item1 = (uint32_t)hitems.size();
+    }
+    if (ditems) dev_free(ctx, ditems, ditems_bytes);
+    ditems = nullptr;
+    ditems_bytes = std::max<size_t>(hitems.size(), 1) * sizeof(uint2);
+    int st = dev_alloc(ctx, reinterpret_cast<void**>(&ditems), ditems_bytes);
+    if (st != ED_OK) {
+      ditems_bytes = 0;
+      return st;
+    }
+    ED_TRY_CUDA(cudaMemcpy(djobs, hjobs.data(), sizeof(JobDev) * hjobs.size(), cudaMemcpyHostToDevice));
+    ED_TRY_CUDA(cudaMemcpy(ditems, hitems.data(), sizeof(uint2) * hitems.size(), cudaMemcpyHostToDevice));
+    chunk = c;
+    return ED_OK;
+  }
   void release() {
     for (auto& a : allocs) dev_free(ctx, a.first, a.second);
     allocs.clear();
+    if (ditems) dev_free(ctx, ditems, ditems_bytes);
+    ditems = nullptr;
     for (auto& s : sectors) free_sector(s.get());
     sectors.clear();
     if (stream) cudaStreamDestroy(stream);
@@ -400,6 +427,7 @@ int batch_run(Batch* bt, const ed_lanczos_opts* o, double* evals, int* iters, ed
   B.jobs = bt->djobs;
   B.items = bt->ditems;
   B.n_items = (uint32_t)bt->hitems.size();
+  B.chunk = bt->chunk;
   B.n_jobs = J;
   B.tot = bt->tot;
   B.ms = ms;
@@ -588,23 +616,18 @@ extern "C" int ed_batch_create(ed_ctx* ctx, const ed_model* model, int n_sectors
     jd.db = s->dn.basis;
     jd.off = off;
     jd.dim = s->dim;
-    jd.item0 = (uint32_t)b.hitems.size();
-    for (uint64_t e = 0; e < s->dim; e += kChunk) b.hitems.push_back(make_uint2((unsigned)q, (unsigned)e));
-    jd.item1 = (uint32_t)b.hitems.size();
     b.hjobs.push_back(jd);
     off += (s->dim + 31) & ~(uint64_t)31;
     b.sectors.push_back(std::move(s));
   }
   b.tot = off;
   int st = b.alloc(&b.djobs, b.hjobs.size());
-  if (st == ED_OK) st = b.alloc(&b.ditems, b.hitems.size());
+  if (st == ED_OK) st = b.set_chunk(kChunkDefault);
   if (st != ED_OK) {
     b.release();
     return st;
   }
-  if (cudaMemcpy(b.djobs, b.hjobs.data(), sizeof(JobDev) * b.hjobs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b.ditems, b.hitems.data(), sizeof(uint2) * b.hitems.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess) {
     b.release();
     set_error("batch set-up copy failed");
     return ED_ERR_CUDA;
@@ -621,6 +644,65 @@ extern "C" int ed_batch_destroy(ed_batch* h) {
   return ED_OK;
 }
 
+namespace ed {
+namespace {
+int batch_dispatch(Batch* b, const ed_lanczos_opts* opts, double* evals, int* iters, ed_batch_info* info,
+                   cudaStream_t user) {
+  switch (b->prec) {
+    case ED_PREC_FP64: return batch_run<PolF64>(b, opts, evals, iters, info, user);
+    case ED_PREC_DF64: return batch_run<PolDF>(b, opts, evals, iters, info, user);
+    default: return batch_run<PolF32>(b, opts, evals, iters, info, user);
+  }
+}
+bool chunk_ok(int c) { return c >= 64 && c <= 65536 && (c & (c - 1)) == 0; }
+}  // namespace
+}  // namespace ed
+
+extern "C" int ed_batch_set_chunk(ed_batch* h, int chunk) {
+  if (!h) ED_INVALID("NULL argument");
+  if (!chunk_ok(chunk)) ED_INVALID("chunk %d is not a power of two in 64..65536", chunk);
+  ED_TRY_CUDA(cudaSetDevice(h->b.ctx->device));
+  ED_TRY_CUDA(cudaStreamSynchronize(h->b.stream));
+  return h->b.set_chunk((uint32_t)chunk);
+}
+
+extern "C" int ed_batch_autotune(ed_batch* h, int steps, ed_batch_tune_result* out, void* stream) {
+  if (!h || !out) ED_INVALID("NULL argument");
+  steps = std::max(2, std::min(steps, 64));
+  Batch* b = &h->b;
+  ED_TRY_CUDA(cudaSetDevice(b->ctx->device));
+  std::memset(out, 0, sizeof(*out));
+  out->chosen = -1;
+  const int cand[] = {256, 512, 1024, 2048, 4096, 8192, 16384, 32768};
+  // a few graph-replayed Lanczos steps of every sector (never converging)
+  ed_lanczos_opts o{};
+  o.k = 1;
+  o.tol = 1e-300;
+  o.max_iter = steps;
+  o.check_every = steps;
+  o.seed = 1;
+  o.reorth = 1;
+  std::vector<double> ev(b->n_jobs);
+  double best = 0.0;
+  for (int c : cand) {
+    const int i = out->n_candidates++;
+    out->chunk[i] = c;
+    out->ms_per_step[i] = -1.0;
+    ED_TRY(b->set_chunk((uint32_t)c));
+    ed_batch_info info{};
+    const int st = batch_dispatch(b, &o, ev.data(), nullptr, &info, as_stream(stream));
+    if (st != ED_OK && st != ED_ERR_NOT_CONVERGED) return st;
+    ED_TRY_CUDA(cudaStreamSynchronize(b->stream));
+    out->ms_per_step[i] = info.total_ms / std::max(1, info.steps);
+    if (out->chosen < 0 || out->ms_per_step[i] < best) {
+      best = out->ms_per_step[i];
+      out->chosen = i;
+    }
+  }
+  set_error("");
+  return b->set_chunk((uint32_t)out->chunk[out->chosen]);
+}
+
 extern "C" int ed_batch_lanczos(ed_batch* h, const ed_lanczos_opts* opts, double* evals, int* iters,
                                 ed_batch_info* info, void* stream) {
   if (!h || !opts || !evals) ED_INVALID("NULL argument");
@@ -635,12 +717,7 @@ extern "C" int ed_batch_lanczos(ed_batch* h, const ed_lanczos_opts* opts, double
   ED_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   cudaEventRecord(ev, user);
   cudaStreamWaitEvent(b->stream, ev, 0);
-  int st;
-  switch (b->prec) {
-    case ED_PREC_FP64: st = batch_run<PolF64>(b, opts, evals, iters, info, user); break;
-    case ED_PREC_DF64: st = batch_run<PolDF>(b, opts, evals, iters, info, user); break;
-    default: st = batch_run<PolF32>(b, opts, evals, iters, info, user);
-  }
+  const int st = batch_dispatch(b, opts, evals, iters, info, user);
   cudaEventRecord(ev, b->stream);
   cudaStreamWaitEvent(user, ev, 0);
   cudaEventDestroy(ev);

@@ -73,3 +73,36 @@ def test_fp32_vectors_batch(env):
             assert abs(ev[q, 0] - ref[0]) <= 1e-6 * abs(ref[0]), (a, bb, ev[q, 0], ref[0])
     finally:
         ed.ed_batch_destroy(b)
+
+
+def test_sector_packing_chunks_and_tuner(env):
+    """Eigenvalues do not depend on how sectors are cut into work items (beyond
+    the order of sums); the packing tuner reports every candidate and keeps the
+    fastest; bad chunk sizes are rejected."""
+    ed, ctx, torch = env
+    m = W.kanamori(8, seed=1)
+    secs = [(a, b) for a in range(2, 7) for b in range(2, 7)]
+    b = ed.ed_batch_create(ctx, m, secs, "fp64")
+    try:
+        res = {}
+        for c in (64, 1024, 8192):
+            ed.ed_batch_set_chunk(b, c)
+            ev, it, info, st = ed.ed_batch_lanczos(b, len(secs), k=3, tol=1e-11, max_iter=200, check_every=5)
+            res[c] = ev
+        for c in (64, 8192):
+            assert np.nanmax(np.abs(res[c] - res[1024])) <= 1e-10
+        for q, (a, bb) in enumerate(secs[:6]):
+            ref = oracle_lowest(m, a, bb, 3)
+            assert np.max(np.abs(res[1024][q, :len(ref)] - ref)) <= 1e-10 * max(1, np.max(np.abs(ref)))
+        r = ed.ed_batch_autotune(b, steps=8)
+        ms = np.array(r.ms_per_step[:r.n_candidates])
+        assert r.n_candidates == 8 and np.all(ms > 0)
+        assert r.chosen == int(np.argmin(ms))
+        assert list(r.chunk[:8]) == [256, 512, 1024, 2048, 4096, 8192, 16384, 32768]
+        ev, it, info, st = ed.ed_batch_lanczos(b, len(secs), k=3, tol=1e-11, max_iter=200, check_every=5)
+        assert np.nanmax(np.abs(ev - res[1024])) <= 1e-10
+        for bad in (0, 100, 32, 131072):
+            with pytest.raises(ed.EdError):
+                ed.ed_batch_set_chunk(b, bad)
+    finally:
+        ed.ed_batch_destroy(b)
