@@ -795,9 +795,9 @@ int launch_pair(const Sector* s, const void* x, void* y, cudaStream_t st, double
 // H*v variants of the fast path: up strings per block (one: k_apply_win, two:
 // k_apply_pair) times a launch shape (threads per block, the blocks per SM the
 // register budget is sized for; shared memory may allow fewer).
-constexpr int kNShapes = 4;
-constexpr int kShapeBS[kNShapes] = {256, 192, 256, 512};
-constexpr int kShapeMinB[kNShapes] = {3, 4, 2, 1};
+constexpr int kNShapes = 5;
+constexpr int kShapeBS[kNShapes] = {256, 192, 256, 512, 384};
+constexpr int kShapeMinB[kNShapes] = {3, 4, 2, 1, 2};
 
 template <class P>
 int run_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
@@ -806,13 +806,15 @@ int run_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st,
     case 1: return launch_fast<P, 192, 4>(s, x, y, st, dotp, nparts);
     case 2: return launch_fast<P, 256, 2>(s, x, y, st, dotp, nparts);
     case 3: return launch_fast<P, 512, 1>(s, x, y, st, dotp, nparts);
+    case 4: return launch_fast<P, 384, 2>(s, x, y, st, dotp, nparts);
   }
   if constexpr (P::prec != ED_PREC_FP64) {
     switch (v) {
-      case 4: return launch_pair<P, 256, 3>(s, x, y, st, dotp, nparts);
-      case 5: return launch_pair<P, 192, 4>(s, x, y, st, dotp, nparts);
-      case 6: return launch_pair<P, 256, 2>(s, x, y, st, dotp, nparts);
-      case 7: return launch_pair<P, 512, 1>(s, x, y, st, dotp, nparts);
+      case 5: return launch_pair<P, 256, 3>(s, x, y, st, dotp, nparts);
+      case 6: return launch_pair<P, 192, 4>(s, x, y, st, dotp, nparts);
+      case 7: return launch_pair<P, 256, 2>(s, x, y, st, dotp, nparts);
+      case 8: return launch_pair<P, 512, 1>(s, x, y, st, dotp, nparts);
+      case 9: return launch_pair<P, 384, 2>(s, x, y, st, dotp, nparts);
     }
   }
   ED_INVALID("H*v variant %d does not apply to this sector", v);

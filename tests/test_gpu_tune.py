@@ -25,6 +25,8 @@ def env():
     ed.ed_ctx_destroy(ctx)
 
 
+NV = 10  # fast H*v variants: one or two up strings per block x five launch shapes
+
 CASES = [("Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6),
          ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7),
          ("AIM N_s=13 (7,6)", lambda: W.aim(13, seed=3), 7, 6),
@@ -43,11 +45,12 @@ def test_variants_agree_bitwise_and_tuner_picks_fastest(env, name, mk, nu, nd, p
     try:
         xd = to_dev(x, prec, ed, torch)
         outs = {}
-        for v in range(8):
+        nv = NV
+        for v in range(nv):
             try:
                 ed.ed_sector_set_variant(sec, v)
             except ed.EdError:
-                assert prec == "fp64" and v >= 4   # two-row variants exist for DF64 and FP32 only
+                assert prec == "fp64" and v >= nv // 2   # two-row variants exist for DF64 and FP32 only
                 continue
             assert ed.ed_sector_get_variant(sec) == v
             y = empty_vec(dim, prec, ed, torch)
@@ -64,16 +67,16 @@ def test_variants_agree_bitwise_and_tuner_picks_fastest(env, name, mk, nu, nd, p
         assert rel_err(got, ref) <= TOL[prec]
 
         r = ed.ed_sector_autotune(sec, reps=3)
-        assert r.n_candidates == 8
-        ms = np.array(r.ms[:8])
+        assert r.n_candidates == nv
+        ms = np.array(r.ms[:nv])
         fit = ms > 0
-        assert fit[:4].any()
+        assert fit[:nv // 2].any()
         if prec == "fp64":
-            assert not fit[4:].any()
+            assert not fit[nv // 2:].any()
         assert r.chosen == int(np.argmin(np.where(fit, ms, np.inf)))
         assert ed.ed_sector_get_variant(sec) == r.chosen
         assert ed.ed_sector_get_info(sec).kernel == r.kernel[r.chosen]
-        assert [r.kernel[i] for i in range(8)] == [2, 2, 2, 2, 3, 3, 3, 3]
+        assert [r.kernel[i] for i in range(nv)] == [2] * (nv // 2) + [3] * (nv // 2)
     finally:
         ed.ed_sector_destroy(sec)
 
@@ -136,7 +139,7 @@ def test_nothing_to_tune_and_bad_variants(env):
         ed.ed_sector_destroy(g)
     s = ed.ed_sector_create(ctx, m, 6, 6, "fp64")
     try:
-        for bad in (4, 8, -2, 100):
+        for bad in (NV // 2, NV, -2, 100):
             with pytest.raises(ed.EdError):
                 ed.ed_sector_set_variant(s, bad)
         ed.ed_sector_set_variant(s, -1)
