@@ -44,7 +44,7 @@ def args_parse(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="df64", choices=["df64", "fp64", "fp32"])
-    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-steps", type=int, default=30)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--no-autotune", action="store_true", help="time the untuned default H*v variant")
@@ -277,31 +277,59 @@ def run_ours(a):
     ms_step = total_ms / a.steps
     nbytes = alg_bytes(a.prec, dim)
 
-    # end to end: pinned host x -> device, H*v, device -> pinned host y
+    # end to end: pinned host x -> device, H*v, device -> pinned host y, every
+    # step.  Steps are pipelined on three streams with two device buffers each
+    # way: the copy-in of step i+1 and the copy-out of step i-1 overlap the
+    # H*v of step i (the host link carries both directions at once).
     h2d = d2h = dim * (4 if a.prec == "fp32" else 8)
-    hx = torch.empty(dim * epv, dtype=tdt, pin_memory=True)
-    hx.copy_(x.cpu())
-    hy = torch.empty_like(hx, pin_memory=True)
-    for _ in range(2):
-        x.copy_(hx, non_blocking=True)
-        ed.ed_apply_h(sec, x, y, stream)
-        hy.copy_(y, non_blocking=True)
+    hx = [torch.empty(dim * epv, dtype=tdt, pin_memory=True) for _ in range(2)]
+    hy = [torch.empty(dim * epv, dtype=tdt, pin_memory=True) for _ in range(2)]
+    for h in hx:
+        h.copy_(x.cpu())
+    xd = [x, torch.empty_like(x)]
+    yd = [y, torch.empty_like(y)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+
+    def pipeline(n):
+        h2d_done = [torch.cuda.Event() for _ in range(2)]
+        app_done = [torch.cuda.Event() for _ in range(2)]
+        d2h_done = [torch.cuda.Event() for _ in range(2)]
+        for i in range(n):
+            b = i % 2
+            with torch.cuda.stream(s_in):
+                if i >= 2:
+                    s_in.wait_event(app_done[b])        # step i-2 finished reading xd[b]
+                xd[b].copy_(hx[b], non_blocking=True)
+                h2d_done[b].record(s_in)
+            s_cmp.wait_event(h2d_done[b])
+            if i >= 2:
+                s_cmp.wait_event(d2h_done[b])           # step i-2's result has left yd[b]
+            ed.ed_apply_h(sec, xd[b], yd[b], s_cmp)
+            app_done[b].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(app_done[b])
+                hy[b].copy_(yd[b], non_blocking=True)
+                d2h_done[b].record(s_out)
+
+    pipeline(4)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(a.e2e_steps):
-        x.copy_(hx, non_blocking=True)
-        ed.ed_apply_h(sec, x, y, stream)
-        hy.copy_(y, non_blocking=True)
-    e1.record(stream)
+    e0.record(s_in)
+    s_cmp.wait_event(e0)
+    s_out.wait_event(e0)
+    pipeline(a.e2e_steps)
+    s_out.wait_stream(s_in)
+    s_out.wait_stream(s_cmp)
+    e1.record(s_out)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
     ms_step, e2e_ms = ranks_max([ms_step, e2e_ms], dist, "cuda")
     value = whole_job_gbs(world, nbytes, ms_step)
     e2e = {"value": whole_job_gbs(world, nbytes, e2e_ms), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-           "what": "pinned host x -> device, ed_apply_h, device -> pinned host y, per step"}
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": a.e2e_steps,
+           "what": "pinned host x -> device, ed_apply_h, device -> pinned host y, every step; steps pipelined "
+                   "on three streams (copy-in of step i+1 and copy-out of step i-1 overlap H*v of step i)"}
 
     extras = {}
     if not a.no_extras and rank == 0:
