@@ -62,3 +62,23 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch):
     with contextlib.redirect_stdout(out):
         bench.run_reference(bench.args_parse([]))
     assert out.getvalue() == ""
+
+
+def test_reference_arm_json_line(monkeypatch):
+    """bench.py --impl reference on rank 0: one JSON line with the base
+    contract's keys, the oracle as the CPU baseline, and an e2e with no copies."""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        bench.run_reference(bench.args_parse(["--impl", "reference", "--steps", "1", "--warmup", "0"]))
+    lines = [l for l in out.getvalue().splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GB/s"
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("three-orbital Kanamori impurity, N_s=15")
