@@ -175,6 +175,7 @@ int ed_ctx_create(int device, size_t hbm_budget, ed_ctx** out) {
   c.num_sms = prop.multiProcessorCount;
   c.device_name = prop.name;
   c.smem_optin = prop.sharedMemPerBlockOptin;
+  c.smem_per_sm = prop.sharedMemPerMultiprocessor;
   int st = dev_alloc_n(&c, &c.d_binom, 33 * 33);
   if (st == ED_OK) st = dev_alloc_n(&c, &c.d_red, kRedSlots);
   if (st == ED_OK && cudaMallocHost(&c.h_red, 4096) != cudaSuccess) {
@@ -223,7 +224,6 @@ int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn, int
   ed_sector* h = new ed_sector();
   int st = build_sector(&ctx->c, model, n_up, n_dn, prec, &h->s);
   if (st == ED_OK && !(flags & ED_SECTOR_GENERIC)) st = build_fast(&h->s);
-  if (st == ED_OK) tune_apply_cached(&h->s);
   if (st == ED_OK && (flags & ED_SECTOR_CSR)) st = build_csr(&h->s);
   if (st != ED_OK) {
     free_sector(&h->s);

@@ -985,6 +985,7 @@ int build_fast(Sector* s) {
   }
   ED_TRY_CUDA(cudaStreamSynchronize(0));  // legacy stream only: leaves other work running
   f.ok = true;
+  tune_apply_cached(s);  // a variant tuned earlier for this shape (any creator: ABI, server, Green's function)
   return ED_OK;
 }
 
@@ -1001,9 +1002,21 @@ bool fast_variant_applies(const Sector* s, int v) {
   return v < kNShapes || s->fast.pair_ok;
 }
 
-// Untuned choice: two rows per block for float vectors, one otherwise.
+// Untuned choice: two rows per block for float vectors, one otherwise; 256
+// threads x 3 blocks per SM while three staged blocks fit the SM's shared
+// memory, else 384 x 2 (24 warps either way; measured at N_s = 16, where
+// 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
-  return (s->prec == ED_PREC_FP32 && s->fast.pair_ok) ? kNShapes : 0;
+  const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;
+  const uint32_t D = s->dn.D;
+  const int nc = s->fast.n_coef;
+  size_t smem = 0;
+  if (pair) smem = pair_smem<PolF32>(D, nc);
+  else if (s->prec == ED_PREC_FP64) smem = fast_smem<PolF64>(D, nc);
+  else smem = fast_smem<PolDF>(D, nc);
+  const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
+  const bool three = 3 * (smem + 1024) <= per_sm;  // 1 KB reserved per block
+  return (pair ? kNShapes : 0) + (three ? 0 : 4);   // shape 0: 256 x 3, shape 4: 384 x 2
 }
 
 int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp,

@@ -54,6 +54,7 @@ struct Ctx {
   std::atomic<size_t> in_use{0};
   int num_sms = 0;
   size_t smem_optin = 0;
+  size_t smem_per_sm = 0;        // shared memory of one SM (all resident blocks)
   uint32_t* d_binom = nullptr;   // [33][33] binomial coefficients C(n, k)
   double* d_red = nullptr;       // reduction scratch (partials), kRedSlots doubles
   double* h_red = nullptr;       // pinned host mirror of d_red[0..63]
