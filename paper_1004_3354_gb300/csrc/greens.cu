@@ -74,6 +74,7 @@ struct SectorCache {
     }
     std::unique_ptr<Sector> s(new Sector());
     int st = build_sector(ctx, m, nu, nd, prec, s.get());
+    if (st == ED_OK) st = build_fast(s.get());  // the fast row kernel where the sector allows it
     if (st != ED_OK) {
       free_sector(s.get());
       return st;

@@ -164,3 +164,29 @@ def test_spectral_weight_and_bad_frequencies(env):
     for bad in ([0.5 + 0.0j], [0.5 - 0.1j], [complex(np.nan, 0.1)]):
         with pytest.raises(ed.EdError):
             ed.ed_greens_cf_z(ctx, m, "fp64", dstates, np.array(bad), 40.0, orbital=m.orb0, spin=0, depth=10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_fast_kernel_sectors(env, prec):
+    """AIM N_s = 12: the N+1 and N-1 sectors of the continued fractions are
+    large enough for the fast row kernel; G agrees with the oracle's CF from the
+    same ground-state vector."""
+    ed, ctx, torch = env
+    m = W.aim(12, seed=3)
+    for nu, nd in ((7, 6), (5, 6)):
+        s = ed.ed_sector_create(ctx, m, nu, nd, prec)
+        assert ed.ed_sector_get_info(s).kernel == 2
+        ed.ed_sector_destroy(s)
+    sec = ed.ed_sector_create(ctx, m, 6, 6, "fp64")
+    try:
+        n = 924 * 924
+        v = torch.empty(n, dtype=torch.float64, device="cuda")
+        ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-11, max_iter=400, reorth=False, evecs=v)
+    finally:
+        ed.ed_sector_destroy(sec)
+    vh = v.cpu().numpy()
+    beta, nw, depth = 40.0, 256, 40
+    ref = og.greens_cf(m, [(6, 6, float(ev[0]), vh)], beta, nw, m.orb0, 0, depth=depth)
+    dv = to_dev(vh, prec, ed, torch)
+    G = ed.ed_greens_cf(ctx, m, prec, [(6, 6, float(ev[0]), dv)], beta, nw, orbital=m.orb0, spin=0, depth=depth)
+    assert np.max(np.abs(G - ref)) <= 1e-8, np.max(np.abs(G - ref))
