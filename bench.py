@@ -603,8 +603,24 @@ def run_solve15(a):
             r["max_abs_G_err_vs_fp64"] = float(np.max(np.abs(G - ref_G)))
             r["max_abs_A_err_vs_fp64"] = float(np.max(np.abs(A - ref_A)))
         out["results"][prec] = r
-    # stored CSR vs matrix-free, FP64
+    # set-up (the T_setup of Table 1): sector tables, fast row-kernel tables, stored CSR
+    setup = {}
+    for ns, nu, nd in ((15, 7, 8), (16, 8, 8)):
+        mm = W.kanamori(ns, seed=SEED)
+        for label, flags in (("tables", ed.ED_SECTOR_GENERIC), ("tables+fast", 0)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sx = ed.ed_sector_create(ctx, mm, nu, nd, "df64", flags)
+            torch.cuda.synchronize()
+            setup[f"ns{ns}_{label}_s"] = time.perf_counter() - t0
+            ed.ed_sector_destroy(sx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     sec = ed.ed_sector_create(ctx, m, NUP, NDN, "fp64", ed.ED_SECTOR_CSR)
+    torch.cuda.synchronize()
+    setup["ns15_tables+fast+csr_s"] = time.perf_counter() - t0
+    out["setup"] = setup
+    # stored CSR vs matrix-free, FP64
     info = ed.ed_sector_get_info(sec)
     x = torch.from_numpy(W.random_vector(dim, seed=1)).cuda()
     y1, y2 = torch.empty_like(x), torch.empty_like(x)
