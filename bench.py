@@ -12,8 +12,14 @@ Prints one JSON line (rank 0).  Replicas only: with --gpus N under torchrun each
 rank runs the same workload on its own GPU, no collective on the data path
 (weak scaling); value = sum over ranks of bytes / max-over-ranks time.
 
---impl reference times the CPU oracle (the reference arm of this build) on a
-bounded row sample of the same workload on the host cores.
+--impl reference times the CPU oracle (the reference arm: the paper has no
+code to run) on a bounded row sample of the same workload on the host cores.
+
+Other workloads (--workload): sectors12 (all 169 sectors of N_s = 12, batched),
+solve15 (ground state, G(i w_n), spectral function, set-up, stored CSR),
+serve (a stream of impurity solves through the request server), lowest8
+(eight lowest states, full basis vs thick restart), dmft (ED/DMFT of the
+square-lattice Hubbard model).
 """
 from __future__ import annotations
 
