@@ -72,6 +72,27 @@ def workload_config(prec, dim):
             "model": "kanamori U=2.3 J=0.4 U'=U-2J J'=J, eps_k~U[-1.5,1.5], V~U[0.1,0.4], seed 0"}
 
 
+# Arithmetic ceiling of one H*v.  Multiply-adds per element: the off-diagonal
+# entries of the row plus two for the diagonal (e_dn + W and e_up).  A
+# double-float multiply-add is 12 FP32 instructions (10 when x is a float);
+# FP64 rows take one DFMA.  Peaks from the unit counts at the 2.07 GHz maximum
+# SM clock: 152 SMs x 128 FP32 lanes; 152 SMs x 2 DFMA per clock.
+FP32_PEAK = 152 * 128 * 2.07e9
+DFMA_PEAK = 152 * 2 * 2.07e9
+
+
+def alu_roofline(prec, dim, nnz_per_row, launch_ms):
+    macs = dim * (nnz_per_row + 1.0)
+    if prec == "fp64":
+        ops, peak, unit = macs, DFMA_PEAK, "T DFMA/s"
+    else:
+        ops, peak, unit = macs * (12 if prec == "df64" else 10), FP32_PEAK, "T FP32 instructions/s"
+    achieved = ops / (launch_ms * 1e-3)
+    return {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak / 1e12, 3), "unit": unit,
+            "frac": round(achieved / peak, 4), "ops_per_launch": ops, "macs_per_element": nnz_per_row + 1.0,
+            "peak_source": "unit counts x 2.07 GHz maximum SM clock"}
+
+
 def ranks_max(vals, dist, device):
     """Each timing (ms) maximised over ranks, so that whole-job rates are set by
     the slowest rank; identity on one rank."""
@@ -382,6 +403,7 @@ def run_ours(a):
                      "kernel": kernel_name, "variant": variant, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": nbytes, "median_launch_ms": statistics.median(launch_ms),
                      "apply_src_sha": sha},
+        "alu_roofline": alu_roofline(a.prec, dim, info.nnz_per_row, statistics.mean(launch_ms)),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
         "clocks": clk, "nnz_per_row": round(info.nnz_per_row, 3), "other_formats": extras, "autotune": tuned,
     }
