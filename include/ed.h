@@ -2,12 +2,14 @@
  * ed.h -- C ABI of the GB300 exact-diagonalisation library (libedgb.so).
  *
  * The library applies the Hamiltonian of an impurity or cluster model to a
- * vector inside one (N_up, N_dn) particle-number sector, runs Lanczos for the
- * lowest eigenpairs and evaluates continued-fraction Matsubara Green's
- * functions, all on one GPU.  The problem is the one arXiv 1004.3354 solves:
- * diagonalise the impurity Hamiltonian for its lowest states (Sec. 2, after
- * Eq. 3) with a Lanczos/Arnoldi solver built on repeated H*v (Sec. 3), then
- * form G(i w_n) (Eq. 3).
+ * vector inside one (N_up, N_dn) particle-number sector, runs Lanczos (full
+ * basis, three-vector, or thick-restart) for the lowest eigenpairs, evaluates
+ * continued-fraction Green's functions at Matsubara or real frequencies and
+ * one DMFT self-consistency update, all on one GPU; sectors can be solved in
+ * batches and impurity solves served as a request stream.  The problem is the
+ * one arXiv 1004.3354 solves: diagonalise the impurity Hamiltonian for its
+ * lowest states (Sec. 2, after Eq. 3) with a Lanczos/Arnoldi solver built on
+ * repeated H*v (Sec. 3), then form G(i w_n) (Eq. 3) for the DMFT loop (Sec. 2).
  *
  * Conventions shared by every call
  *  - Every call returns an ed_status.  ED_OK is 0.  On error, ed_last_error()
@@ -109,8 +111,9 @@ typedef struct ed_sector_info {
   uint64_t csr_nnz;             /* stored CSR entries (0 without ED_SECTOR_CSR) */
   uint64_t table_bytes;         /* device bytes held by the sector */
   double   nnz_per_row;         /* mean stored entries per row of H (diagonal included) */
-  int      kernel;              /* H*v kernel: 0 flat, 1 row-staged generic, 2 fast row kernel,
-                                   3 fast two-row kernel (FP32 vectors) */
+  int      kernel;              /* H*v kernel in use: 0 flat, 1 row-staged generic, 2 fast row
+                                   kernel, 3 fast two-row kernel (the FP32 default; DF64 when
+                                   the autotuner picks it) */
 } ed_sector_info;
 
 /* ------------------------------------------------------------------ errors */
