@@ -20,7 +20,12 @@
 //    the zero coefficient.
 //  * With the impurity orbitals on the top sites, down strings come in blocks
 //    of equal impurity pattern and a spin-flip / pair-hop move shifts the rank
-//    by a per-pattern constant, read from a small shared table.
+//    by a per-pattern constant, read from a small shared table.  At the start
+//    of a row one warp builds, per impurity pattern, a term list: the row's up
+//    hops followed by the spin-flip / pair-hop entries that apply to that
+//    pattern, with the shift folded into the offset and the sign into the
+//    coefficient.  A window whose strings share one pattern (most of them)
+//    then gathers all its global terms in one loop, two at a time.
 #include <algorithm>
 #include <climits>
 #include <functional>
@@ -65,17 +70,21 @@ struct FastView {
   const double* mx_val;
   const float2* mx_val_df;
   const uint8_t* mx_mv;
+  int n_lp;                     // term lists per row: 2^M with the delta layout, else 1
+  uint32_t lcap;                // capacity of one list: longest up-hop plus spin-flip / pair-hop list
   double* dotp;                 // optional: per-block partial sums of <x, y>
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <class P>
-size_t fast_smem(uint32_t D, int n_coef) {
+size_t fast_smem(uint32_t D, int n_coef, int n_lp, uint32_t lcap) {
   using V = typename P::V;
   using C = typename P::C;
-  return align16(D * sizeof(V)) + align16(n_coef * sizeof(C)) + 2 * align16(kList * sizeof(C)) +
-         2 * align16(kList * sizeof(uint64_t)) + align16(kList * 4) + align16(kMaxDelta * 4);
+  const size_t nl = (size_t)n_lp * lcap;
+  return align16(D * sizeof(V)) + align16(n_coef * sizeof(C)) + align16(nl * sizeof(C)) + align16(kList * sizeof(C)) +
+         align16(nl * sizeof(int64_t)) + align16(kList * sizeof(uint64_t)) + align16(kList * 4) +
+         align16(kMaxDelta * 4) + align16((size_t)n_lp * 4);
 }
 
 // four consecutive table entries (16-byte aligned)
@@ -126,17 +135,25 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
   p += align16(D * sizeof(V));
   C* cs = reinterpret_cast<C*>(p);
   p += align16(F.n_coef * sizeof(C));
-  C* lc = reinterpret_cast<C*>(p);          // up-hop coefficients
-  p += align16(kList * sizeof(C));
+  const uint32_t lcap = F.lcap;
+  const size_t nl = (size_t)F.n_lp * lcap;
+  // term lists of the row, one per impurity pattern p (a single list without
+  // the delta layout): the up hops, then the spin-flip / pair-hop entries that
+  // apply to every down string of pattern p, with the pattern's rank shift
+  // folded into the offset and its sign into the coefficient
+  C* lc = reinterpret_cast<C*>(p);
+  p += align16(nl * sizeof(C));
   C* mc = reinterpret_cast<C*>(p);          // mixed coefficients
   p += align16(kList * sizeof(C));
-  uint64_t* lr = reinterpret_cast<uint64_t*>(p);  // up-hop row offsets (elements)
-  p += align16(kList * sizeof(uint64_t));
+  int64_t* lr = reinterpret_cast<int64_t*>(p);    // element offsets of the list terms
+  p += align16(nl * sizeof(int64_t));
   uint64_t* mr = reinterpret_cast<uint64_t*>(p);  // mixed row offsets
   p += align16(kList * sizeof(uint64_t));
   uint32_t* mm = reinterpret_cast<uint32_t*>(p);  // mixed move offsets
   p += align16(kList * 4);
   int32_t* mds = reinterpret_cast<int32_t*>(p);   // move shifts per pattern
+  p += align16(kMaxDelta * 4);
+  int* ln = reinterpret_cast<int*>(p);            // list lengths
   __shared__ int n_up_s, n_mx_s;
   __shared__ uint32_t pat_s;
   const bool mixd = F.dpat4 != nullptr;
@@ -155,8 +172,43 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
     for (uint32_t d = threadIdx.x; d < D; d += BS) cp_async_elem(xs + d, xr + d);
     const uint32_t h0 = F.uh_ptr[u], nh = F.uh_ptr[u + 1] - h0;
     for (uint32_t k = threadIdx.x; k < nh; k += BS) {
-      lr[k] = (uint64_t)F.uh_tgt[h0 + k] * D;
-      lc[k] = P::ld(F.uh_val, F.uh_val_df, h0 + k);
+      const int64_t off = (int64_t)F.uh_tgt[h0 + k] * D;
+      const C c = P::ld(F.uh_val, F.uh_val_df, h0 + k);
+      for (int q = 0; q < F.n_lp; ++q) {
+        lr[q * lcap + k] = off;
+        lc[q * lcap + k] = c;
+      }
+    }
+    if (mixd && warp == NWARP - 1) {
+      // list q gets, after the up hops and in entry order, the row's spin-flip /
+      // pair-hop entries (at most kList = 64) that apply to impurity pattern q
+      const uint32_t m0 = F.mx_ptr[u], nmr = F.mx_ptr[u + 1] - m0;
+      const uint32_t ja = lane, jb = lane + 32;
+      const bool va = ja < nmr, vb = jb < nmr;
+      const int64_t ta = va ? (int64_t)F.mx_tgt[m0 + ja] * D : 0;
+      const int64_t tb = vb ? (int64_t)F.mx_tgt[m0 + jb] * D : 0;
+      const C ca = va ? P::ld(F.mx_val, F.mx_val_df, m0 + ja) : C{};
+      const C cb = vb ? P::ld(F.mx_val, F.mx_val_df, m0 + jb) : C{};
+      const uint32_t qa = va ? (uint32_t)F.mx_mv[m0 + ja] * (uint32_t)F.np : 0u;
+      const uint32_t qb = vb ? (uint32_t)F.mx_mv[m0 + jb] * (uint32_t)F.np : 0u;
+      const uint32_t below = (1u << lane) - 1u;
+      for (int q = 0; q < F.n_lp; ++q) {
+        const int32_t mda = va ? mds[qa + q] : INT_MIN, mdb = vb ? mds[qb + q] : INT_MIN;
+        const unsigned ba = __ballot_sync(0xffffffffu, mda != INT_MIN);
+        const unsigned bb = __ballot_sync(0xffffffffu, mdb != INT_MIN);
+        const uint32_t base = q * lcap + nh;
+        if (mda != INT_MIN) {
+          const uint32_t at = base + __popc(ba & below);
+          lr[at] = ta + (mda >> 1);
+          lc[at] = (mda & 1) ? P::neg(ca) : ca;
+        }
+        if (mdb != INT_MIN) {
+          const uint32_t at = base + __popc(ba) + __popc(bb & below);
+          lr[at] = tb + (mdb >> 1);
+          lc[at] = (mdb & 1) ? P::neg(cb) : cb;
+        }
+        if (lane == 0) ln[q] = (int)(nh + __popc(ba) + __popc(bb));
+      }
     }
     uint32_t nm = 0;
     if (F.mx_ptr) {
@@ -183,13 +235,16 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
     for (uint32_t w = warp; w < F.n_win; w += NWARP) {
       const uint32_t ent = w * 32 + lane;   // this lane's four entries
       const uint4 dq = __ldg(F.perm4 + ent);
+      // padding entries read at the window's first string (lane 0, slot 0,
+      // always a real one), so every term of the window's list stays in bounds
+      const uint32_t d0 = __shfl_sync(0xffffffffu, dq.x, 0);
       uint32_t dv[4];
       bool ok[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const uint32_t d = sel4(dq, e);
         ok[e] = d < D;
-        dv[e] = ok[e] ? d : 0u;
+        dv[e] = ok[e] ? d : d0;
       }
       C dg[4];
       ld4<C>(ddr + 4 * (uint64_t)ent, dg);
@@ -229,50 +284,42 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
         }
 #undef ED_HOP
       }
-      // up hops, two neighbour rows at a time
+      // the row's term list, two terms at a time: up hops and, in a window
+      // whose strings share one impurity pattern, that pattern's spin-flip /
+      // pair-hop terms
+      const uint32_t wp = mixd ? F.wpat[w] : 0xffffffffu;
+      const bool uni = wp != 0xffffffffu;
       {
+        const int nlw = uni ? ln[wp] : nup;
+        const int64_t* lrw = lr + (uni ? wp * lcap : 0u);
+        const C* lcw = lc + (uni ? wp * lcap : 0u);
         int k = 0;
-        for (; k + 1 < nup; k += 2) {
-          const V* x0 = x + lr[k];
-          const V* x1 = x + lr[k + 1];
+        for (; k + 1 < nlw; k += 2) {
+          const V* x0 = x + lrw[k];
+          const V* x1 = x + lrw[k + 1];
           V a0[4], a1[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             a0[e] = __ldg(x0 + dv[e]);
             a1[e] = __ldg(x1 + dv[e]);
           }
-          const C c0 = lc[k], c1 = lc[k + 1];
+          const C c0 = lcw[k], c1 = lcw[k + 1];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             P::mac(acc[e], c0, a0[e]);
             P::mac(acc[e], c1, a1[e]);
           }
         }
-        if (k < nup) {
-          const V* x0 = x + lr[k];
-          const C c0 = lc[k];
+        if (k < nlw) {
+          const V* x0 = x + lrw[k];
+          const C c0 = lcw[k];
 #pragma unroll
           for (int e = 0; e < 4; ++e) P::mac(acc[e], c0, __ldg(x0 + dv[e]));
         }
       }
-      // spin-flip / pair-hop
-      if (nmx) {
-        const uint32_t wp = mixd ? F.wpat[w] : 0xffffffffu;
-        if (wp != 0xffffffffu) {
-          // every string of the window has impurity pattern wp: one shift per entry
-          for (int j = 0; j < nmx; ++j) {
-            const int32_t md = mds[mm[j] + wp];
-            if (md == INT_MIN) continue;
-            const V* xm = x + mr[j] + (md >> 1);
-            const C cj = (md & 1) ? P::neg(mc[j]) : mc[j];
-            V xv[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) xv[e] = ok[e] ? __ldg(xm + dv[e]) : xs[0];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (ok[e]) P::mac(acc[e], cj, xv[e]);
-          }
-        } else if (mixd) {
+      // spin-flip / pair-hop in the other windows
+      if (nmx && !uni) {
+        if (mixd) {
           const uint32_t pd4 = __ldg(F.dpat4 + ent);
           for (int j = 0; j < nmx; ++j) {
             const V* xm = x + mr[j];
@@ -753,6 +800,8 @@ FastView make_view(const Sector* s) {
   F.mx_val = s->mx_val;
   F.mx_val_df = s->mx_val_df;
   F.mx_mv = s->mx_mv;
+  F.n_lp = f.n_lp;
+  F.lcap = f.lcap;
   return F;
 }
 
@@ -760,7 +809,7 @@ template <class P, int BS, int MINB>
 int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts) {
   FastView F = make_view<P>(s);
   F.dotp = dotp;
-  size_t smem = fast_smem<P>(F.D, F.n_coef);
+  size_t smem = fast_smem<P>(F.D, F.n_coef, F.n_lp, F.lcap);
   auto kern = k_apply_win<P, BS, MINB>;
   ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -857,10 +906,12 @@ int build_fast(Sector* s) {
   const size_t vbytes = elem_bytes(s->prec);
   if ((uint64_t)D * vbytes >= (1ull << 19)) return ED_OK;
   const int nc = (int)coef.size();
-  if (std::max(fast_smem<PolF64>(D, nc), fast_smem<PolDF>(D, nc)) > 220 * 1024) return ED_OK;
+  const bool mix_delta = s->dn_move && s->orb0 + s->M == s->n_s && s->M * s->M * (1 << s->M) <= kMaxDelta;
+  const int n_lp = mix_delta ? 1 << s->M : 1;
+  const uint32_t lcap = std::max(1u, s->up.max_hops + (mix_delta ? s->max_mix : 0u));
+  if (std::max(fast_smem<PolF64>(D, nc, n_lp, lcap), fast_smem<PolDF>(D, nc, n_lp, lcap)) > 220 * 1024) return ED_OK;
   const size_t smem2 = s->prec == ED_PREC_DF64 ? pair_smem<PolDF>(D, nc) : pair_smem<PolF32>(D, nc);
   const bool pair = s->prec != ED_PREC_FP64 && (uint64_t)D * 2 * vbytes < (1ull << 19) && smem2 <= 220 * 1024;
-  const bool mix_delta = s->dn_move && s->orb0 + s->M == s->n_s && s->M * s->M * (1 << s->M) <= kMaxDelta;
 
   // window-local order: inside each window of 128 ranks, longest hop list first
   const uint32_t n_win = (D + kWin - 1) / kWin;
@@ -930,6 +981,8 @@ int build_fast(Sector* s) {
   f.max_cnt = std::max(1u, s->dn.max_hops);
   f.n_coef = (int)coef.size();
   f.n_pat = 1 << wbits;
+  f.n_lp = n_lp;
+  f.lcap = lcap;
   const uint64_t NE = (uint64_t)n_win * kWin;
   ED_TRY(sector_alloc(s, &f.perm, NE));
   ED_TRY(sector_alloc(s, &f.cnt, (size_t)n_win * 4));
@@ -1012,8 +1065,8 @@ int fast_default_variant(const Sector* s) {
   const int nc = s->fast.n_coef;
   size_t smem = 0;
   if (pair) smem = pair_smem<PolF32>(D, nc);
-  else if (s->prec == ED_PREC_FP64) smem = fast_smem<PolF64>(D, nc);
-  else smem = fast_smem<PolDF>(D, nc);
+  else if (s->prec == ED_PREC_FP64) smem = fast_smem<PolF64>(D, nc, s->fast.n_lp, s->fast.lcap);
+  else smem = fast_smem<PolDF>(D, nc, s->fast.n_lp, s->fast.lcap);
   const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
   const bool three = 3 * (smem + 1024) <= per_sm;  // 1 KB reserved per block
   return (pair ? kNShapes : 0) + (three ? 0 : 4);   // shape 0: 256 x 3, shape 4: 384 x 2

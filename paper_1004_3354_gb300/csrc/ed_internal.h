@@ -167,6 +167,8 @@ struct Sector {
     uint8_t* dpat = nullptr;        // [n_win*128] impurity pattern of each entry
     uint32_t* wpat = nullptr;       // [n_win] pattern shared by a whole window, or ~0u
     int32_t* mdelta = nullptr;      // [M*M][2^M] (shift << 1 | sign) or INT32_MIN
+    int n_lp = 1;                   // term lists per row in the row kernel (2^M with mix_delta)
+    uint32_t lcap = 1;              // entries of one list: longest up-hop + spin-flip/pair-hop list
     // two-row kernel (double-float and float vectors): rows are processed in
     // pairs (row_order[2i], row_order[2i+1]) staged interleaved; its hop words
     // hold byte offsets into that interleaved row and into a table of 16-byte
