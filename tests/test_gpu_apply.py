@@ -151,6 +151,32 @@ def test_apply_n15_half_filling_sampled(env, prec):
     assert rel_err(y[rows], ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_apply_n15_window_edges(env, prec):
+    """N_s=15 (7,8): every element of the row kernel's 128-string windows that
+    span two impurity patterns (spin-flip / pair-hop shifts differ inside the
+    window) and of the padded last window (6435 = 50*128 + 35), on the first,
+    the last and 40 random up rows, checked against the oracle."""
+    ed, ctx, torch = env
+    m = W.kanamori(15, seed=0)
+    nu, nd = 7, 8
+    dbas = osec.spin_basis(15, nd)
+    D = len(dbas)
+    dim = D * D
+    pat = (dbas >> np.uint64(15 - 3)).astype(np.int64)  # impurity orbitals are the top sites
+    starts = np.nonzero(np.diff(pat))[0] + 1            # first rank of each new pattern block
+    wins = sorted({int(b) // 128 for b in starts if int(b) % 128} | {(D - 1) // 128})
+    ds = np.concatenate([np.arange(w * 128, min(D, (w + 1) * 128)) for w in wins])
+    assert len(wins) >= 2 and D % 128 != 0
+    us = np.unique(np.concatenate([[0, D - 1], np.random.default_rng(11).integers(0, D, 40)]))
+    rows = (us[:, None] * D + ds[None, :]).ravel()
+    x = W.random_vector(dim, seed=7)
+    xin = input_for(prec, x)
+    y = run_apply(ed, ctx, torch, m, nu, nd, prec, x, expect_kernel=fast_kernel(2, prec))
+    ref = osec.apply_rows(m, nu, nd, rows, xin)
+    assert rel_err(y[rows], ref) <= TOL[prec], rel_err(y[rows], ref)
+
+
 def test_apply_csr_variant(env):
     ed, ctx, torch = env
     for m, nu, nd in ((W.aim(6), 3, 3), (W.kanamori(10, seed=6), 5, 5)):
