@@ -128,6 +128,41 @@ def check_dmft_noninteracting():
     assert abs(((z ** 3) * (gl - 1.0 / z))[-1].real - 4 * t * t) < 1e-3
 
 
+def check_dmft_lattice_moments():
+    """Lattice G at chemical potential mu and a constant self-energy s: since
+    1/(z + mu - s - e) = 1/z + (e - mu + s)/z^2 + ..., the band's moments
+    (m1 = 0, m2 = 4 t^2) give z G = 1 + (s - mu)/z + (4 t^2 + (s - mu)^2)/z^2 + O(z^-3)."""
+    from oracle import dmft
+    t, mu, s = 0.5, 0.3, -0.45
+    e, w = W.square_lattice_energies(t, 128)
+    z = 1j * np.array([1000.0, 2000.0])  # the O(z^-3) remainder is ~3e-9 here
+    for sig in (0.0, s):
+        gl = dmft.lattice_gloc(z, np.full(2, sig), mu, e, w)
+        a = sig - mu
+        ref = 1.0 + a / z + (4 * t * t + a * a) / z ** 2
+        assert np.max(np.abs(z * gl - ref)) < 2e-8, np.max(np.abs(z * gl - ref))
+
+
+def check_dmft_weiss_field():
+    """The Weiss field closes the loop: for any G, inserting the impurity
+    self-energy of a bath and the same G as the local one gives that bath's
+    hybridisation back; at U = 0 and mu = 0 the new hybridisation of the square
+    lattice has first moment 4 t^2 (z Delta_new -> sum V^2 = 4 t^2)."""
+    from oracle import dmft
+    iw = 1j * greens.matsubara(25.0, 48)
+    eps, V = np.array([-0.8, 0.2, 1.1]), np.array([0.3, 0.45, 0.2])
+    G = 1.0 / (iw - 0.15 - 0.6 / iw + 0.2j)  # any G without zeros
+    sig = dmft.self_energy(iw, G, 0.1, eps, V)
+    back = dmft.weiss_hybridisation(iw, sig, G, 0.1)
+    assert np.max(np.abs(back - dmft.hybridisation(iw, eps, V))) < 1e-12
+    t = 0.5
+    e, w = W.square_lattice_energies(t, 128)
+    z = 1j * np.array([400.0])
+    gl = dmft.lattice_gloc(z, np.zeros(1), 0.0, e, w)
+    dn = dmft.weiss_hybridisation(z, np.zeros(1), gl, 0.0)
+    assert abs((z * dn)[0].real - 4 * t * t) < 1e-4 and abs((z * dn)[0].imag) < 1e-6, z * dn
+
+
 def check_dmft_bath_fit_recovers_bath():
     """A hybridisation made from a known bath is fitted back (chi2 ~ 0) from a perturbed start."""
     from oracle import dmft
@@ -314,6 +349,7 @@ PINS = [check_two_site_hubbard, check_u0_ground_energy, check_u0_greens, check_t
         check_su2_inclusion, check_cf_vs_lehmann, check_sum_rules, check_fig1_csr,
         check_u0_greens_real_axis, check_spectral_sum_rule, check_cf_vs_lehmann_real_axis,
         check_dmft_atomic_self_energy, check_dmft_noninteracting, check_dmft_bath_fit_recovers_bath,
+        check_dmft_lattice_moments, check_dmft_weiss_field,
         check_sector_dims, check_tiers_agree, check_row_sampling]
 
 
@@ -426,3 +462,38 @@ def test_mistake_rank_off_by_one(monkeypatch):
     orig = sector.spin_basis
     monkeypatch.setattr(sector, "spin_basis", lambda n_s, n: orig(n_s, n)[::-1].copy())
     assert _fails(check_sector_dims)
+
+
+def test_mistake_dmft_self_energy_sign(monkeypatch):
+    from oracle import dmft
+
+    def wrong(z, G_imp, eps_d, eps, V):
+        z = np.asarray(z, dtype=complex)
+        return z - eps_d - dmft.hybridisation(z, eps, V) + 1.0 / np.asarray(G_imp)
+    monkeypatch.setattr(dmft, "self_energy", wrong)
+    assert _fails(check_dmft_atomic_self_energy)
+
+
+def test_mistake_dmft_dropped_hybridisation(monkeypatch):
+    from oracle import dmft
+
+    def wrong(z, G_imp, eps_d, eps, V):
+        return np.asarray(z, dtype=complex) - eps_d - 1.0 / np.asarray(G_imp)
+    monkeypatch.setattr(dmft, "self_energy", wrong)
+    assert _fails(check_dmft_noninteracting)
+
+
+def test_mistake_dmft_mu_sign(monkeypatch):
+    from oracle import dmft
+    orig = dmft.lattice_gloc
+    monkeypatch.setattr(dmft, "lattice_gloc", lambda z, sigma, mu, e, w: orig(z, sigma, -mu, e, w))
+    assert _fails(check_dmft_lattice_moments)
+
+
+def test_mistake_dmft_weiss_sigma_sign(monkeypatch):
+    from oracle import dmft
+
+    def wrong(z, sigma, G_loc, eps_d):
+        return np.asarray(z, dtype=complex) - eps_d + np.asarray(sigma) - 1.0 / np.asarray(G_loc)
+    monkeypatch.setattr(dmft, "weiss_hybridisation", wrong)
+    assert _fails(check_dmft_weiss_field)
