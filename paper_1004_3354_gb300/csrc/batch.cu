@@ -161,34 +161,108 @@ __global__ void __launch_bounds__(kBT) k_b_dot(BatchDev B, const V* __restrict__
   }
 }
 
-// partial[k * n_items + it] = <V_k, w>, k <= j
+// Sixteen-byte vectors of elements for the CGS2 kernels: four FP32, two DF64
+// or two FP64 elements per load.  Vector slots and sector offsets are padded
+// to 32 elements and work items start at multiples of the chunk, so every
+// item starts 16-byte aligned.
+template <class V>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+  __device__ static __forceinline__ float get(const T& v, int i) { return (&v.x)[i]; }
+  __device__ static __forceinline__ void set(T& v, int i, float x) { (&v.x)[i] = x; }
+};
+template <>
+struct Vec16<float2> {
+  using T = float4;
+  static constexpr int N = 2;
+  __device__ static __forceinline__ float2 get(const T& v, int i) {
+    return i ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+  }
+  __device__ static __forceinline__ void set(T& v, int i, float2 x) {
+    if (i) v.z = x.x, v.w = x.y;
+    else v.x = x.x, v.y = x.y;
+  }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+  __device__ static __forceinline__ double get(const T& v, int i) { return (&v.x)[i]; }
+  __device__ static __forceinline__ void set(T& v, int i, double x) { (&v.x)[i] = x; }
+};
+
+// Block sums of up to kKB accumulators with one barrier: each warp reduces
+// every accumulator (butterfly), then warp q reduces accumulator q over the
+// warps in the same butterfly order as bblock_sum; lane 0 of warp q stores it.
+template <class A>
+__device__ __forceinline__ void bblock_sum_group(A (&acc)[kKB], int nq, double* out, uint64_t stride) {
+  __shared__ A sh[kKB][kBT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // the previous group's readers are done with sh
+#pragma unroll
+  for (int q = 0; q < kKB; ++q) {
+    A v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v = badd(v, bshfl(v, o));
+    if (lane == 0) sh[q][w] = v;
+  }
+  __syncthreads();
+  static_assert(kBT / 32 >= kKB, "one warp per accumulator");
+  if (w < nq) {
+    A v = (lane < kBT / 32) ? sh[w][lane] : A{};
+    for (int o = 16; o > 0; o >>= 1) v = badd(v, bshfl(v, o));
+    if (lane == 0) out[(uint64_t)w * stride] = bd(v);
+  }
+}
+
+// partial[k * n_items + it] = <V_k, w>, k <= j.  Sixteen-byte loads keep
+// (kKB + 1) x 16 bytes per thread in flight; the item's ragged tail (fewer
+// than one vector) is read element by element.
 template <class V>
 __global__ void __launch_bounds__(kBT) k_b_multidot(BatchDev B, const V* __restrict__ Vb, const V* __restrict__ w) {
   using A = typename BAcc<V>::T;
+  using W16 = Vec16<V>;
+  using VT = typename W16::T;
+  constexpr int N = W16::N;
   const int j = *B.step;
   for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
     const uint2 item = B.items[it];
     const bool on = B.active[item.x] != 0;
     const JobDev& J = B.jobs[item.x];
-    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
+    const uint64_t e0 = J.off + item.y;
+    const uint64_t n = min((uint64_t)item.y + B.chunk, J.dim) - item.y;
+    const uint64_t nv = n / N;
+    const VT* wv = reinterpret_cast<const VT*>(w + e0);
     for (int k0 = 0; k0 <= j; k0 += kKB) {
+      const int nq = min(kKB, j + 1 - k0);
       A acc[kKB];
 #pragma unroll
       for (int q = 0; q < kKB; ++q) acc[q] = A{};
       if (on) {
-        for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) {
-          const V we = w[J.off + e];
+        const V* vk = Vb + (uint64_t)k0 * B.tot + e0;
+        for (uint64_t t = threadIdx.x; t < nv; t += kBT) {
+          const VT wq = wv[t];
+          VT vq[kKB];
 #pragma unroll
           for (int q = 0; q < kKB; ++q)
-            if (k0 + q <= j) bmac(acc[q], Vb[(uint64_t)(k0 + q) * B.tot + J.off + e], we);
+            if (q < nq) vq[q] = __ldg(reinterpret_cast<const VT*>(vk + (uint64_t)q * B.tot) + t);
+#pragma unroll
+          for (int q = 0; q < kKB; ++q)
+            if (q < nq) {
+#pragma unroll
+              for (int i = 0; i < N; ++i) bmac(acc[q], W16::get(vq[q], i), W16::get(wq, i));
+            }
+        }
+        for (uint64_t e = nv * N + threadIdx.x; e < n; e += kBT) {
+          const V we = w[e0 + e];
+#pragma unroll
+          for (int q = 0; q < kKB; ++q)
+            if (q < nq) bmac(acc[q], vk[(uint64_t)q * B.tot + e], we);
         }
       }
-#pragma unroll
-      for (int q = 0; q < kKB; ++q) {
-        if (k0 + q > j) break;
-        A r = bblock_sum(acc[q]);
-        if (threadIdx.x == 0) B.partial[(uint64_t)(k0 + q) * B.n_items + it] = bd(r);
-      }
+      bblock_sum_group(acc, nq, B.partial + (uint64_t)k0 * B.n_items + it, B.n_items);
     }
   }
 }
@@ -245,7 +319,6 @@ __global__ void __launch_bounds__(kBT) k_b_finish(BatchDev B, int op) {
 }
 
 // mode 0: w += nal_j V_j + nbe_j V_{j-1}
-// mode 1: w += sum_{k<=j} h_k V_k
 // mode 2: V_{j+1} = inv_{j+1} w        mode 3: V_0 = inv_0 w
 template <class V>
 __global__ void __launch_bounds__(kBT) k_b_axpy(BatchDev B, V* __restrict__ Vb, V* __restrict__ w, int mode) {
@@ -264,16 +337,56 @@ __global__ void __launch_bounds__(kBT) k_b_axpy(BatchDev B, V* __restrict__ Vb, 
         bcmac(a, B.nal_d, B.nal_f, base + j, Vb[(uint64_t)j * B.tot + g]);
         if (j > 0) bcmac(a, B.nbe_d, B.nbe_f, base + j, Vb[(uint64_t)(j - 1) * B.tot + g]);
         w[g] = bstore(a, w);
-      } else if (mode == 1) {
-        A a = bacc_of(w[g]);
-        for (int k = 0; k <= j; ++k) bcmac(a, B.h_d, B.h_f, base + k, Vb[(uint64_t)k * B.tot + g]);
-        w[g] = bstore(a, w);
       } else {
         const int s = (mode == 2) ? j + 1 : 0;
         A a{};
         bcmac(a, B.inv_d, B.inv_f, base + s, w[g]);
         Vb[(uint64_t)s * B.tot + g] = bstore(a, Vb);
       }
+    }
+  }
+}
+
+// CGS2 update w += sum_{k<=j} h_k V_k for every active sector: sixteen-byte
+// loads of w and of each V_k, each element's terms in the order k = 0..j
+// (the ragged tail of an item element by element).
+template <class V>
+__global__ void __launch_bounds__(kBT) k_b_cgs_update(BatchDev B, const V* __restrict__ Vb, V* __restrict__ w) {
+  using A = typename BAcc<V>::T;
+  using W16 = Vec16<V>;
+  using VT = typename W16::T;
+  constexpr int N = W16::N;
+  const int j = *B.step;
+  for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
+    const uint2 item = B.items[it];
+    if (!B.active[item.x]) continue;
+    const JobDev& J = B.jobs[item.x];
+    const size_t base = (size_t)item.x * B.ms;
+    const uint64_t e0 = J.off + item.y;
+    const uint64_t n = min((uint64_t)item.y + B.chunk, J.dim) - item.y;
+    const uint64_t nv = n / N;
+    VT* wv = reinterpret_cast<VT*>(w + e0);
+    const V* v0 = Vb + e0;
+    for (uint64_t t = threadIdx.x; t < nv; t += kBT) {
+      const VT wq = wv[t];
+      A a[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = bacc_of(W16::get(wq, i));
+#pragma unroll 4
+      for (int k = 0; k <= j; ++k) {
+        const VT vq = __ldg(reinterpret_cast<const VT*>(v0 + (uint64_t)k * B.tot) + t);
+#pragma unroll
+        for (int i = 0; i < N; ++i) bcmac(a[i], B.h_d, B.h_f, base + k, W16::get(vq, i));
+      }
+      VT o;
+#pragma unroll
+      for (int i = 0; i < N; ++i) W16::set(o, i, bstore(a[i], w));
+      wv[t] = o;
+    }
+    for (uint64_t e = nv * N + threadIdx.x; e < n; e += kBT) {
+      A a = bacc_of(w[e0 + e]);
+      for (int k = 0; k <= j; ++k) bcmac(a, B.h_d, B.h_f, base + k, v0[(uint64_t)k * B.tot + e]);
+      w[e0 + e] = bstore(a, w);
     }
   }
 }
@@ -492,7 +605,7 @@ int batch_run(Batch* bt, const ed_lanczos_opts* o, double* evals, int* iters, ed
   for (int pass = 0; pass < 2; ++pass) {
     k_b_multidot<V><<<grid, kBT, 0, st>>>(B, Vb, w);
     k_b_finish<<<hgrid, kBT, 0, st>>>(B, BF_NEGH);
-    k_b_axpy<V><<<grid, kBT, 0, st>>>(B, Vb, w, 1);
+    k_b_cgs_update<V><<<grid, kBT, 0, st>>>(B, Vb, w);
   }
   k_b_dot<V><<<grid, kBT, 0, st>>>(B, Vb, w, 1);
   k_b_finish<<<fgrid, kBT, 0, st>>>(B, BF_BETA);
