@@ -281,7 +281,9 @@ typedef struct ed_trlan_info {
   double residual[ED_MAX_K];    /* Ritz residual estimates */
   double apply_ms;              /* device time in H*v (CUDA events) */
   double total_ms;              /* wall time of the call */
-  size_t basis_bytes;           /* device bytes of basis, work vector and rotation target */
+  size_t basis_bytes;           /* device bytes of basis, work vector and rotation target
+                                   (max_basis + 2 + keep slots of dim elements, each slot padded
+                                   to a multiple of 32 elements) */
 } ed_trlan_info;
 
 /* Lowest k eigenvalues (host, ascending; NaN past the sector dimension) and,

@@ -18,6 +18,7 @@
 
 #include "apply_common.h"
 #include "tri_common.h"
+#include "vec16.h"
 
 struct ed_batch;
 
@@ -161,38 +162,9 @@ __global__ void __launch_bounds__(kBT) k_b_dot(BatchDev B, const V* __restrict__
   }
 }
 
-// Sixteen-byte vectors of elements for the CGS2 kernels: four FP32, two DF64
-// or two FP64 elements per load.  Vector slots and sector offsets are padded
-// to 32 elements and work items start at multiples of the chunk, so every
-// item starts 16-byte aligned.
-template <class V>
-struct Vec16;
-template <>
-struct Vec16<float> {
-  using T = float4;
-  static constexpr int N = 4;
-  __device__ static __forceinline__ float get(const T& v, int i) { return (&v.x)[i]; }
-  __device__ static __forceinline__ void set(T& v, int i, float x) { (&v.x)[i] = x; }
-};
-template <>
-struct Vec16<float2> {
-  using T = float4;
-  static constexpr int N = 2;
-  __device__ static __forceinline__ float2 get(const T& v, int i) {
-    return i ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
-  }
-  __device__ static __forceinline__ void set(T& v, int i, float2 x) {
-    if (i) v.z = x.x, v.w = x.y;
-    else v.x = x.x, v.y = x.y;
-  }
-};
-template <>
-struct Vec16<double> {
-  using T = double2;
-  static constexpr int N = 2;
-  __device__ static __forceinline__ double get(const T& v, int i) { return (&v.x)[i]; }
-  __device__ static __forceinline__ void set(T& v, int i, double x) { (&v.x)[i] = x; }
-};
+// The CGS2 kernels read sixteen-byte vectors (vec16.h).  Vector slots and
+// sector offsets are padded to 32 elements and work items start at multiples
+// of the chunk, so every item starts 16-byte aligned.
 
 // Block sums of up to kKB accumulators with one barrier: each warp reduces
 // every accumulator (butterfly), then warp q reduces accumulator q over the

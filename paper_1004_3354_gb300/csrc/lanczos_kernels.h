@@ -12,6 +12,7 @@
 
 #include "ed_internal.h"
 #include "tri_common.h"
+#include "vec16.h"
 
 namespace ed {
 
@@ -111,6 +112,51 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const V* __restrict__ 
 #pragma unroll
     for (int q = 0; q < KB; ++q)
       if (q < kn) dmac(acc[q], Vb[(uint64_t)(k0 + q) * stride + i], wi);
+  }
+  for (int q = 0; q < kn; ++q) {
+    A r = block_reduce(acc[q], sh);
+    if (threadIdx.x == 0) partial[(uint64_t)q * gridDim.x + blockIdx.x] = to_d(r);
+  }
+}
+
+// The same multi-dot with sixteen-byte loads (every slot, and w, 16-byte
+// aligned): (KB + 1) x 16 bytes per thread in flight; the tail of the range
+// element by element.
+template <class V, int KB>
+__global__ void __launch_bounds__(kRedThreads) k_multidot16(const V* __restrict__ Vb, uint64_t stride, int k0,
+                                                            int nvec, const V* __restrict__ w, uint64_t n,
+                                                            double* __restrict__ partial) {
+  using A = typename AccOf<V>::T;
+  using W16 = Vec16<V>;
+  using VT = typename W16::T;
+  constexpr int N = W16::N;
+  __shared__ A sh[32];
+  A acc[KB];
+#pragma unroll
+  for (int q = 0; q < KB; ++q) acc[q] = A{};
+  const int kn = min(KB, nvec - k0);
+  const uint64_t nv = n / N;
+  const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (uint64_t)gridDim.x * blockDim.x;
+  const VT* wv = reinterpret_cast<const VT*>(w);
+  const V* vk = Vb + (uint64_t)k0 * stride;
+  for (uint64_t t = g0; t < nv; t += gs) {
+    const VT wq = wv[t];
+    VT vq[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+      if (q < kn) vq[q] = __ldg(reinterpret_cast<const VT*>(vk + (uint64_t)q * stride) + t);
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+      if (q < kn) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) dmac(acc[q], W16::get(vq[q], i), W16::get(wq, i));
+      }
+  }
+  for (uint64_t i = nv * N + g0; i < n; i += gs) {
+    const V wi = w[i];
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+      if (q < kn) dmac(acc[q], vk[(uint64_t)q * stride + i], wi);
   }
   for (int q = 0; q < kn; ++q) {
     A r = block_reduce(acc[q], sh);
@@ -291,6 +337,41 @@ __global__ void k_multi_axpy(const V* __restrict__ Vb, uint64_t stride, int nvec
   }
 }
 
+// The same update with sixteen-byte loads and stores (slots and w 16-byte
+// aligned); each element's terms in the order k = 0 .. nvec - 1, as above.
+template <class V>
+__global__ void k_multi_axpy16(const V* __restrict__ Vb, uint64_t stride, int nvec, V* __restrict__ w, uint64_t n,
+                               Coefs c) {
+  using A = typename AccOf<V>::T;
+  using W16 = Vec16<V>;
+  using VT = typename W16::T;
+  constexpr int N = W16::N;
+  const uint64_t nv = n / N;
+  const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (uint64_t)gridDim.x * blockDim.x;
+  VT* wv = reinterpret_cast<VT*>(w);
+  for (uint64_t t = g0; t < nv; t += gs) {
+    const VT wq = wv[t];
+    A a[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = acc_of(W16::get(wq, i));
+#pragma unroll 4
+    for (int k = 0; k < nvec; ++k) {
+      const VT vq = __ldg(reinterpret_cast<const VT*>(Vb + (uint64_t)k * stride) + t);
+#pragma unroll
+      for (int i = 0; i < N; ++i) amac(a[i], c.h_d, c.h_f, k, W16::get(vq, i));
+    }
+    VT o;
+#pragma unroll
+    for (int i = 0; i < N; ++i) W16::set(o, i, store_v(a[i], w));
+    wv[t] = o;
+  }
+  for (uint64_t i = nv * N + g0; i < n; i += gs) {
+    auto a = acc_of(w[i]);
+    for (int k = 0; k < nvec; ++k) amac(a, c.h_d, c.h_f, k, Vb[(uint64_t)k * stride + i]);
+    w[i] = store_v(a, w);
+  }
+}
+
 // out = w * inv[slot]
 template <class V>
 __global__ void k_scale(const V* __restrict__ w, V* __restrict__ out, uint64_t n, Coefs c, int slot) {
@@ -402,12 +483,17 @@ int cgs2(Work<V>& W, const V* Vb, uint64_t stride, int nvec, V* w) {
   if (nvec <= 0) return ED_OK;
   constexpr int KB = 8;
   const int nb = (int)std::min<uint64_t>(W.grid, (uint64_t)kRedSlots / KB);
+  // sixteen-byte loads when every slot and w start on a 16-byte boundary
+  const bool v16 = (stride * sizeof(V)) % 16 == 0 && reinterpret_cast<uintptr_t>(Vb) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(w) % 16 == 0;
   for (int pass = 0; pass < 2; ++pass) {
     for (int k0 = 0; k0 < nvec; k0 += KB) {
-      k_multidot<V, KB><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
+      if (v16) k_multidot16<V, KB><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
+      else k_multidot<V, KB><<<nb, kRedThreads, 0, W.st>>>(Vb, stride, k0, nvec, w, W.n, W.partial);
       k_finish<<<std::min(KB, nvec - k0), kRedThreads, 0, W.st>>>(W.partial, nb, OP_NEGH, k0, W.c, 0.0);
     }
-    k_multi_axpy<V><<<W.grid, 256, 0, W.st>>>(Vb, stride, nvec, w, W.n, W.c);
+    if (v16) k_multi_axpy16<V><<<W.grid, 256, 0, W.st>>>(Vb, stride, nvec, w, W.n, W.c);
+    else k_multi_axpy<V><<<W.grid, 256, 0, W.st>>>(Vb, stride, nvec, w, W.n, W.c);
     ED_LAUNCH_CHECK();
   }
   return ED_OK;
@@ -523,10 +609,12 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
   size_t eb = sizeof(V);
   int nvec_store = reorth ? (mmax + 1) : 3;
   DevBuf vb, cb, v0b;
-  ED_TRY(vb.alloc(ctx, ((size_t)nvec_store + 1) * n * eb));
+  // basis slots padded to 32 elements, so that each starts 16-byte aligned
+  const uint64_t ld = pad32(n);
+  ED_TRY(vb.alloc(ctx, ((size_t)nvec_store + 1) * ld * eb));
   ED_TRY(cb.alloc(ctx, coef_bytes(mmax, std::max(kk, 1))));
   V* Vbase = static_cast<V*>(vb.p);
-  V* w = Vbase + (size_t)nvec_store * n;
+  V* w = Vbase + (size_t)nvec_store * ld;
   if (!reorth) ED_TRY(v0b.alloc(ctx, n * eb));
   Carve cv{static_cast<char*>(cb.p)};
   Coefs c = carve_coefs(cv, mmax);
@@ -549,7 +637,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
   if (vgrid == 0) vgrid = 1;
 
   k_init_coefs<<<1, 256, 0, st>>>(c, mmax + 2);
-  auto vec = [&](int j) -> V* { return reorth ? Vbase + (size_t)j * n : Vbase + (size_t)(j % 3) * n; };
+  auto vec = [&](int j) -> V* { return reorth ? Vbase + (size_t)j * ld : Vbase + (size_t)(j % 3) * ld; };
 
   // start vector
   if (o->v0) {
@@ -596,7 +684,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
       ED_TRY(dot_to(W, (const V*)vj, (const V*)w, OP_ALPHA, j));
       k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vj, vjm, n, c, j);
       ED_LAUNCH_CHECK();
-      if (reorth) ED_TRY(cgs2(W, (const V*)Vbase, n, j + 1, w));
+      if (reorth) ED_TRY(cgs2(W, (const V*)Vbase, ld, j + 1, w));
       ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_BETA, j + 1, thr));
       k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(j + 1), n, c, j + 1);
       ED_LAUNCH_CHECK();
@@ -662,7 +750,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
       // new random direction, orthogonalised against V[0..m)
       ++restarts;
       k_random<V><<<vgrid, 256, 0, st>>>(w, n, o->seed + 7919ull * restarts);
-      ED_TRY(cgs2(W, (const V*)Vbase, n, m, w));
+      ED_TRY(cgs2(W, (const V*)Vbase, ld, m, w));
       ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_NORM_INV, 1));
       k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(m), n, c, 1);
       // beta[m] = 0 splits T; reset the exhaustion flag
@@ -692,7 +780,7 @@ int lanczos_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evecs
     V* out = static_cast<V*>(evecs);
     if (reorth) {
       for (int i0 = 0; i0 < kc; i0 += 8)
-        k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vbase, n, m, Sd, Sf, ldS, i0, std::min(8, kc - i0), out, n, 0);
+        k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vbase, ld, m, Sd, Sf, ldS, i0, std::min(8, kc - i0), out, n, 0);
       ED_LAUNCH_CHECK();
     } else {
       // second pass: regenerate v_j with the stored alpha, beta and accumulate

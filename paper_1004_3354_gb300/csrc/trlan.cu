@@ -192,11 +192,13 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
   // basis V[0..m] (m + 1 vectors), w, rotation target T[0..keep)
   const int n_rot = (m >= 3) ? keep : 0;
   DevBuf vb, cb;
-  ED_TRY(vb.alloc(ctx, ((size_t)m + 2 + n_rot) * n * eb));
+  // slots padded to 32 elements, so that each starts 16-byte aligned
+  const uint64_t ld = pad32(n);
+  ED_TRY(vb.alloc(ctx, ((size_t)m + 2 + n_rot) * ld * eb));
   ED_TRY(cb.alloc(ctx, coef_bytes(m, 1) + (size_t)kMaxBasis * kMaxBasis * 8 * 4 + (size_t)kMaxBasis * 8 * 8));
   V* Vb = static_cast<V*>(vb.p);
-  V* w = Vb + (size_t)(m + 1) * n;
-  V* T = w + n;
+  V* w = Vb + (size_t)(m + 1) * ld;
+  V* T = w + ld;  // rotation target, keep vectors of n elements back to back
   Carve cv{static_cast<char*>(cb.p)};
   Coefs c = carve_coefs(cv, m);
   const int ldS = kMaxBasis;
@@ -218,7 +220,7 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
   W.c = c;
   uint32_t vgrid = (uint32_t)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 16);
   if (vgrid == 0) vgrid = 1;
-  auto vec = [&](int j) -> V* { return Vb + (size_t)j * n; };
+  auto vec = [&](int j) -> V* { return Vb + (size_t)j * ld; };
 
   k_init_coefs<<<1, 256, 0, st>>>(c, m + 2);
   if (o->v0) {
@@ -264,7 +266,7 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
       ED_TRY(dot_to(W, (const V*)vec(j), (const V*)w, OP_ALPHA, j));
       k_lz_update<V><<<vgrid, 256, 0, st>>>(w, vec(j), j > l ? vec(j - 1) : nullptr, n, c, j);
       ED_LAUNCH_CHECK();
-      ED_TRY(cgs2(W, (const V*)Vb, n, j + 1, w));
+      ED_TRY(cgs2(W, (const V*)Vb, ld, j + 1, w));
       ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_BETA, j + 1, thr));
       k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(j + 1), n, c, j + 1);
       ED_LAUNCH_CHECK();
@@ -306,7 +308,7 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
         // to the basis, uncoupled from it (beta = 0)
         ++injections;
         k_random<V><<<vgrid, 256, 0, st>>>(w, n, o->seed + 7919ull * (uint64_t)injections);
-        ED_TRY(cgs2(W, (const V*)Vb, n, size, w));
+        ED_TRY(cgs2(W, (const V*)Vb, ld, size, w));
         ED_TRY(dot_to(W, (const V*)w, (const V*)w, OP_NORM_INV, 1));
         k_scale<V><<<vgrid, 256, 0, st>>>(w, vec(size), n, c, 1);
         ED_LAUNCH_CHECK();
@@ -337,9 +339,9 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
       break;
     }
     for (int i0 = 0; i0 < keep; i0 += 8)
-      k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vb, n, m, Sd, Sf, ldS, i0, std::min(8, keep - i0), T, n, 0);
+      k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vb, ld, m, Sd, Sf, ldS, i0, std::min(8, keep - i0), T, n, 0);
     ED_LAUNCH_CHECK();
-    ED_TRY_CUDA(cudaMemcpyAsync(Vb, T, (size_t)keep * n * eb, cudaMemcpyDeviceToDevice, st));
+    ED_TRY_CUDA(cudaMemcpy2DAsync(Vb, ld * eb, T, n * eb, n * eb, keep, cudaMemcpyDeviceToDevice, st));
     ED_TRY_CUDA(cudaMemcpyAsync(vec(keep), vec(m), n * eb, cudaMemcpyDeviceToDevice, st));
     k_tr_keep<<<1, 128, 0, st>>>(theta, Sd, ldS, m, keep, c, th, sv);
     ED_LAUNCH_CHECK();
@@ -356,7 +358,7 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
     // Sd holds the eigenvectors of the last projected matrix (size `size`)
     V* out = static_cast<V*>(evecs);
     for (int i0 = 0; i0 < kc; i0 += 8)
-      k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vb, n, size, Sd, Sf, ldS, i0, std::min(8, kc - i0), out, n, 0);
+      k_ritz<V, 8><<<vgrid, 256, 0, st>>>(Vb, ld, size, Sd, Sf, ldS, i0, std::min(8, kc - i0), out, n, 0);
     ED_LAUNCH_CHECK();
   }
   ED_TRY_CUDA(cudaStreamSynchronize(st));
@@ -366,7 +368,7 @@ int trlan_impl(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed
     info->n_converged = std::min(n_conv, kc);
     for (int i = 0; i < ED_MAX_K; ++i) info->residual[i] = (i < kc) ? h_res[i] : 0.0;
     info->apply_ms = apply_ms;
-    info->basis_bytes = ((size_t)m + 2 + n_rot) * n * eb;
+    info->basis_bytes = ((size_t)m + 2 + n_rot) * ld * eb;
     info->total_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   }
