@@ -144,3 +144,38 @@ def test_invalid_arguments(env):
                 ed.ed_lanczos_tr(sec, **kw)
     finally:
         ed.ed_sector_destroy(sec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+@pytest.mark.parametrize("solver", ["full_basis", "thick_restart"])
+def test_odd_dimension_padded_basis(env, solver, prec):
+    """Kanamori N_s=7 (3,4), dim 35^2 = 1225 (odd, 1 mod 4): the basis slots are
+    padded to 32 elements and the CGS2 kernels read sixteen-byte vectors with
+    an element-wise tail.  8 lowest eigenpairs against dense diagonalisation."""
+    ed, ctx, torch = env
+    m = W.kanamori(7, seed=5)
+    H = osec.build_csr(m, 3, 4)
+    n = H.shape[0]
+    assert n == 1225
+    ref = spectrum.lowest(H, 8)
+    sec = ed.ed_sector_create(ctx, m, 3, 4, prec)
+    try:
+        vecs = empty_vec(n, prec, ed, torch, count=8)
+        tol = 1e-7 if prec == "fp32" else 1e-11
+        if solver == "full_basis":
+            ev, info, st = ed.ed_lanczos(sec, k=8, tol=tol, max_iter=600, evecs=vecs,
+                                         allow_not_converged=(prec == "fp32"))
+        else:
+            ev, info, st = ed.ed_lanczos_tr(sec, k=8, tol=tol, max_basis=24, keep=12, max_iter=4000,
+                                            evecs=vecs, allow_not_converged=(prec == "fp32"))
+        if prec == "fp32":
+            assert np.max(np.abs(ev - ref) / np.abs(ref)) <= 1e-6, (ev, ref)
+            return
+        assert ev_err(ev, ref) <= 1e-10, (ev, ref)
+        V = to_host(vecs, prec, 8 * n, ed, torch).reshape(8, n)
+        for i in range(8):
+            r = H @ V[i] - ev[i] * V[i]
+            assert np.linalg.norm(r) <= 1e-8 * max(1, abs(ev[i])), (i, np.linalg.norm(r))
+        assert np.max(np.abs(V @ V.T - np.eye(8))) < 1e-9
+    finally:
+        ed.ed_sector_destroy(sec)
