@@ -149,14 +149,13 @@ __global__ void __launch_bounds__(kBT) k_b_dot(BatchDev B, const V* __restrict__
   const int j = *B.step;
   for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
     const uint2 item = B.items[it];
+    if (!B.active[item.x]) continue;  // k_b_finish reads no partial of a converged sector
     A acc{};
-    if (B.active[item.x]) {
-      const JobDev& J = B.jobs[item.x];
-      const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
-      const V* a = (mode == 0) ? Vb + (uint64_t)j * B.tot + J.off : w + J.off;
-      const V* b = w + J.off;
-      for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) bmac(acc, a[e], b[e]);
-    }
+    const JobDev& J = B.jobs[item.x];
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
+    const V* a = (mode == 0) ? Vb + (uint64_t)j * B.tot + J.off : w + J.off;
+    const V* b = w + J.off;
+    for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) bmac(acc, a[e], b[e]);
     acc = bblock_sum(acc);
     if (threadIdx.x == 0) B.partial[it] = bd(acc);
   }
@@ -201,7 +200,7 @@ __global__ void __launch_bounds__(kBT) k_b_multidot(BatchDev B, const V* __restr
   const int j = *B.step;
   for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
     const uint2 item = B.items[it];
-    const bool on = B.active[item.x] != 0;
+    if (!B.active[item.x]) continue;  // k_b_finish reads no partial of a converged sector
     const JobDev& J = B.jobs[item.x];
     const uint64_t e0 = J.off + item.y;
     const uint64_t n = min((uint64_t)item.y + B.chunk, J.dim) - item.y;
@@ -212,7 +211,7 @@ __global__ void __launch_bounds__(kBT) k_b_multidot(BatchDev B, const V* __restr
       A acc[kKB];
 #pragma unroll
       for (int q = 0; q < kKB; ++q) acc[q] = A{};
-      if (on) {
+      {
         const V* vk = Vb + (uint64_t)k0 * B.tot + e0;
         for (uint64_t t = threadIdx.x; t < nv; t += kBT) {
           const VT wq = wv[t];
