@@ -130,12 +130,14 @@ def cf_eval(z: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def greens_cf(model, states, beta: float, n_w: int, orbital: int = 0, spin: int = fock.UP,
               depth: int = 150, boltz_cut: float = 1e-5, reorth: bool = False,
-              return_parts: bool = False, z=None):
+              return_parts: bool = False, z=None, build=build_csr):
     """Continued-fraction G(i w_n) (or G(z) at the given complex z) from a list
     of states (n_up, n_dn, E, vector).
 
     Z is the sum of e^{-beta (E - E_min)} over the states passed; states whose
-    factor is below ``boltz_cut`` are left out of the sum over nu."""
+    factor is below ``boltz_cut`` are left out of the sum over nu.  ``build``
+    makes the neighbour sectors' H (``sector.build_csr`` or, for sectors of tens
+    of millions of states, ``sector.build_csr_blocked``)."""
     E = np.array([s[2] for s in states])
     E0 = E.min()
     fac = np.exp(-beta * (E - E0))
@@ -148,7 +150,7 @@ def greens_cf(model, states, beta: float, n_w: int, orbital: int = 0, spin: int 
 
     def ham(a, b):
         if (a, b) not in Hcache:
-            Hcache[(a, b)] = build_csr(model, a, b)
+            Hcache[(a, b)] = build(model, a, b)
         return Hcache[(a, b)]
 
     for (nu_, nd_, En, vec), f in zip(states, fac):

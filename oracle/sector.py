@@ -118,6 +118,25 @@ def row_entries(model, n_up: int, n_dn: int, rows, terms=None):
     return A.indptr.astype(np.int64), A.indices.astype(np.int64), A.data
 
 
+def build_csr_blocked(model, n_up: int, n_dn: int, block: int = 1 << 21, terms=None) -> sp.csr_matrix:
+    """The same sector CSR as ``build_csr``, assembled block of rows by block of
+    rows from ``row_entries`` (each row's <i|H|j> from the adjoint operator
+    products applied to |i>).  Peak memory is one block's entries plus the
+    finished matrix, so sectors of tens of millions of states fit host RAM."""
+    sec = Sector(model.n_s, n_up, n_dn)
+    ptrs, cols, vals = [np.zeros(1, dtype=np.int64)], [], []
+    base = 0
+    for r0 in range(0, sec.dim, block):
+        rows = np.arange(r0, min(sec.dim, r0 + block), dtype=np.int64)
+        p, c, v = row_entries(model, n_up, n_dn, rows, terms)
+        ptrs.append(p[1:] + base)
+        cols.append(c.astype(np.int32))
+        vals.append(v)
+        base += len(v)
+    return sp.csr_matrix((np.concatenate(vals), np.concatenate(cols), np.concatenate(ptrs)),
+                         shape=(sec.dim, sec.dim))
+
+
 def apply_rows(model, n_up: int, n_dn: int, rows, x: np.ndarray, terms=None) -> np.ndarray:
     """(H x)[rows] for a sector too large to build: y_i = sum_j <i|H|j> x_j."""
     ptr, cols, vals = row_entries(model, n_up, n_dn, rows, terms)
