@@ -35,8 +35,15 @@
  *                    value hi + lo (8 bytes, |lo| <= ulp(hi)); arithmetic in
  *                    error-free float transformations (about 2^-46 relative).
  *                    Values must lie within float's exponent range.
- *      ED_PREC_FP32  float storage; every product and sum formed in
- *                    double-float, the result rounded once to float.
+ *      ED_PREC_FP32  float storage.  The fast H*v path (natural-order
+ *                    kernel) sums each element in float in two passes
+ *                    (diagonal and down hops; up hops, spin-flip and pair-hop)
+ *                    with coefficients rounded to float and adds the two
+ *                    partial sums with one rounding: an element with n terms
+ *                    is within about (n + 3) 2^-24 sum_j |H_ij x_j| of the
+ *                    exact value.  The other H*v kernels (general models) form
+ *                    every product and sum in double-float and round once.
+ *                    Dot products and norms accumulate in double-float.
  */
 #ifndef ED_H
 #define ED_H
@@ -112,8 +119,9 @@ typedef struct ed_sector_info {
   uint64_t table_bytes;         /* device bytes held by the sector */
   double   nnz_per_row;         /* mean stored entries per row of H (diagonal included) */
   int      kernel;              /* H*v kernel in use: 0 flat, 1 row-staged generic, 2 fast row
-                                   kernel, 3 fast two-row kernel (the FP32 default; DF64 when
-                                   the autotuner picks it) */
+                                   kernel, 3 fast two-row kernel (DF64 when the autotuner picks
+                                   it; FP32 where 4 does not apply), 4 natural-order float kernel
+                                   (the FP32 default) */
 } ed_sector_info;
 
 /* ------------------------------------------------------------------ errors */
@@ -126,7 +134,14 @@ int ed_abi_version(void);
 /* Bind the calling thread to `device` and create a context whose own device
  * allocations (tables, Lanczos workspaces) may not exceed hbm_budget bytes
  * (0 = no limit beyond the device).  Errors: ED_ERR_INVALID (no such device),
- * ED_ERR_CUDA. */
+ * ED_ERR_CUDA.
+ * A context holds one reduction scratch buffer (device partial sums and a
+ * pinned host result word) that ed_dot, ed_lanczos, ed_lanczos_tr and the
+ * Green's-function calls of that context all use, whatever stream they are
+ * given: calls on one context must therefore be serialised (one thread and one
+ * stream at a time, or the caller's own ordering between streams).  Use one
+ * context per concurrent caller; the request server keeps private scratch per
+ * request for this reason. */
 int ed_ctx_create(int device, size_t hbm_budget, ed_ctx** out);
 int ed_ctx_destroy(ed_ctx* ctx);
 /* Bytes of device memory currently held by the context and its sectors. */
@@ -188,9 +203,15 @@ int ed_dot(ed_ctx* ctx, const void* x, const void* y, uint64_t n, int prec, doub
  * ED_ERR_INVALID before any device work.  It calls no cudaMalloc or cudaFree.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the one array and each call
- * overwrites it, so calls that overlap on the GPU (other streams or threads)
- * race and must be serialised by the caller. */
+ * any stream capture.  With CUDA's lazy module loading (the default since CUDA
+ * 12.2) that first look-up is also what loads the library module holding the
+ * array onto the device, so the array's 512 KB become resident at the first
+ * call, not when the library is loaded: a caller that will later hand all free
+ * device memory to another framework should make one call (n = 1 is enough)
+ * before doing so.  Later calls change the device's free memory by nothing.
+ * All calls on a device share the one array and each call overwrites it, so
+ * calls that overlap on the GPU (other streams or threads) race and must be
+ * serialised by the caller. */
 int ed_dot_noalloc(const void* x, const void* y, uint64_t n, int prec, double* result, void* stream);
 
 /* ----------------------------------------------------------------- Lanczos */
@@ -227,7 +248,8 @@ int ed_lanczos(ed_sector* s, const ed_lanczos_opts* opts, double* evals,
 typedef struct ed_tune_result {
   int n_candidates;               /* variants tried, in the order of the arrays */
   int chosen;                     /* index of the fastest, now the sector's H*v; -1: nothing to choose */
-  int kernel[ED_MAX_TUNE];        /* 2: one up string per block, 3: two up strings per block */
+  int kernel[ED_MAX_TUNE];        /* 2: one up string per block, 3: two up strings per block,
+                                     4: natural-order float kernel, two or four up strings per block */
   int block[ED_MAX_TUNE];         /* threads per block */
   int min_blocks[ED_MAX_TUNE];    /* blocks per SM the register budget is sized for */
   double ms[ED_MAX_TUNE];         /* median device time of one H*v; -1 where it does not apply or fit */
