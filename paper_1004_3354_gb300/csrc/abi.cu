@@ -273,7 +273,7 @@ int ed_sector_get_info(const ed_sector* h, ed_sector_info* out) {
     }
   }
   int fk = 0, fb = 0, fm = 0;
-  if (s.fast.ok) fast_variant_info(fast_variant_applies(&s, s.tune) ? s.tune : fast_default_variant(&s), &fk, &fb, &fm);
+  if (s.fast.ok) fast_variant_info(s.prec, fast_variant_applies(&s, s.tune) ? s.tune : fast_default_variant(&s), &fk, &fb, &fm);
   out->kernel = s.fast.ok ? fk : ((s.dn.D >= 1024 && (size_t)s.dn.D * elem_bytes(s.prec) <= 96 * 1024) ? 1 : 0);
   out->nnz_per_row = 1.0 + (double)s.dn.n_hops / std::max<uint32_t>(s.dn.D, 1) +
                      (double)s.up.n_hops / std::max<uint32_t>(s.up.D, 1) + mix;

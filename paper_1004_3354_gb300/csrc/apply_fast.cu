@@ -1038,28 +1038,53 @@ int build_fast(Sector* s) {
   }
   ED_TRY_CUDA(cudaStreamSynchronize(0));  // legacy stream only: leaves other work running
   f.ok = true;
+  ED_TRY(build_nat(s, coef, zero_id));
   tune_apply_cached(s);  // a variant tuned earlier for this shape (any creator: ABI, server, Green's function)
   return ED_OK;
 }
 
-int fast_variants() { return 2 * kNShapes; }
+// Variant index: [0, 5) single-row kernel, [5, 10) two-row kernel (launch
+// shapes of kShapeBS / kShapeMinB), [10, 16) natural-order kernel
+// (apply_nat.cu).  Float sectors with natural-order tables use only the last
+// group, whose float sums differ from the double-float sums of the others;
+// double-float sectors may use all three (the natural-order kernel sums in
+// another order, within the format's rounding).  Within each group every
+// variant gives the same y bit for bit.
+constexpr int kNatBase = 2 * kNShapes;
 
-void fast_variant_info(int v, int* kernel, int* block, int* min_blocks) {
+int fast_variants() { return kNatBase + kNatVariants; }
+
+void fast_variant_info(int prec, int v, int* kernel, int* block, int* min_blocks) {
+  if (v >= kNatBase) {
+    int rows = 0;
+    nat_variant_info(prec, v - kNatBase, &rows, block, min_blocks);
+    *kernel = 4;
+    return;
+  }
   *kernel = v < kNShapes ? 2 : 3;
   *block = kShapeBS[v % kNShapes];
   *min_blocks = kShapeMinB[v % kNShapes];
 }
 
 bool fast_variant_applies(const Sector* s, int v) {
-  if (!s->fast.ok || v < 0 || v >= 2 * kNShapes) return false;
+  if (!s->fast.ok || v < 0 || v >= fast_variants()) return false;
+  if (v >= kNatBase) return s->fast.nat_ok;
+  // float sectors with natural-order tables keep its float sums whatever the tuning
+  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) return false;
   return v < kNShapes || s->fast.pair_ok;
 }
 
-// Untuned choice: two rows per block for float vectors, one otherwise; 256
+// Untuned choice: the natural-order kernel for float sectors that have it, four
+// rows per block while two such blocks fit an SM's shared memory, else two;
+// otherwise two rows per block for float vectors, one otherwise; 256
 // threads x 3 blocks per SM while three staged blocks fit the SM's shared
 // memory, else 384 x 2 (24 warps either way; measured at N_s = 16, where
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
+  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
+    const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
+    return kNatBase + (2 * (nat_variant_smem(s, 0) + 1024) <= per_sm ? 0 : 3);
+  }
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;
   const uint32_t D = s->dn.D;
   const int nc = s->fast.n_coef;
@@ -1075,6 +1100,7 @@ int fast_default_variant(const Sector* s) {
 int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp,
                        int* nparts) {
   if (!fast_variant_applies(s, v)) ED_INVALID("H*v variant %d does not apply to this sector", v);
+  if (v >= kNatBase) return launch_nat(s, v - kNatBase, x, y, st, dotp, nparts);
   switch (s->prec) {
     case ED_PREC_FP64: return run_variant<PolF64>(s, v, x, y, st, dotp, nparts);
     case ED_PREC_DF64: return run_variant<PolDF>(s, v, x, y, st, dotp, nparts);

@@ -175,6 +175,16 @@ struct Sector {
     // coefficient entries
     bool pair_ok = false;
     uint32_t* hop2 = nullptr;   // [n_win][max_cnt][32][4] two-row encoding
+    // natural-order kernel for float vectors (apply_nat.cu): lane l of a warp
+    // owns down string 32 g + l, R up strings per block
+    bool nat_ok = false;
+    uint32_t nat_grp = 0;           // ceil(D_dn / 32)
+    uint32_t* nat_hop = nullptr;    // [nat_grp][max_cnt][32]: target rank << 8 | coefficient id
+    uint32_t* nat_meta = nullptr;   // [nat_grp*32]: hop count | diagonal pattern << 8 | impurity pattern << 16
+    float* nat_edn = nullptr;       // [nat_grp*32] e_dn as float
+    float* nat_coef = nullptr;      // [n_coef] down-hop coefficients as float
+    float* nat_W = nullptr;         // [n_pat][n_pat] cross diagonal table as float
+    float2* nat_dd = nullptr;       // [n_pat][nat_grp*32] double-float e_dn[d] + W[pu][pattern(d)] (DF64)
   } fast;
   // autotuned H*v variant of the fast path (apply_fast.cu), -1 = untuned
   int tune = -1;
@@ -218,9 +228,18 @@ int apply_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double*
 std::string tune_key(const Sector* s);
 void tune_apply_cached(Sector* s);
 
+// Natural-order kernel for float and double-float sectors (apply_nat.cu):
+// tables, launch of variant v in [0, kNatVariants), its rows per block /
+// launch shape (they depend on the sector's format) and shared memory.
+constexpr int kNatVariants = 6;
+int build_nat(Sector* s, const std::vector<double>& coef, int zero_id);
+int launch_nat(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp, int* nparts);
+void nat_variant_info(int prec, int v, int* rows, int* block, int* min_blocks);
+size_t nat_variant_smem(const Sector* s, int v);
+
 // Variants of the fast H*v path (apply_fast.cu): index v in [0, fast_variants()).
 int fast_variants();
-void fast_variant_info(int v, int* kernel, int* block, int* min_blocks);
+void fast_variant_info(int prec, int v, int* kernel, int* block, int* min_blocks);
 bool fast_variant_applies(const Sector* s, int v);
 int fast_default_variant(const Sector* s);
 int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp = nullptr,

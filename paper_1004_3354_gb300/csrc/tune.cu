@@ -91,7 +91,7 @@ int autotune(Sector* s, int reps, ed_tune_result* out, cudaStream_t st) {
   double best = 0.0;
   for (int v = 0; v < nv; ++v) {
     const int i = out->n_candidates++;
-    fast_variant_info(v, &out->kernel[i], &out->block[i], &out->min_blocks[i]);
+    fast_variant_info(s->prec, v, &out->kernel[i], &out->block[i], &out->min_blocks[i]);
     out->ms[i] = -1.0;
     if (!fast_variant_applies(s, v)) continue;
     // a launch shape that does not fit the SM is reported and skipped
@@ -138,8 +138,9 @@ int tune_cache_save(Ctx* c, const char* path) {
   f << "{\"format\": \"libedgb-autotune-1\", \"device\": \"" << json_escape(c->device_name) << "\", \"entries\": [";
   bool first = true;
   for (const auto& kv : c->tune_cache) {
-    int k = 0, bs = 0, mb = 0;
-    fast_variant_info(kv.second, &k, &bs, &mb);
+    int k = 0, bs = 0, mb = 0, prec = 0;
+    std::sscanf(kv.first.c_str(), "prec=%d", &prec);  // the key starts with the sector's format
+    fast_variant_info(prec, kv.second, &k, &bs, &mb);
     f << (first ? "\n" : ",\n") << "  {\"key\": \"" << json_escape(kv.first) << "\", \"variant\": " << kv.second
       << ", \"kernel\": " << k << ", \"block\": " << bs << ", \"min_blocks\": " << mb << "}";
     first = false;

@@ -25,7 +25,29 @@ def env():
     ed.ed_ctx_destroy(ctx)
 
 
-NV = 10  # fast H*v variants: one or two up strings per block x five launch shapes
+# fast H*v variants: [0, 5) one up string per block (kernel 2), [5, 10) two up
+# strings per block (kernel 3), both x five launch shapes; [10, 16) the
+# natural-order kernel (kernel 4) for float and double-float vectors, two or
+# four (float) / one or two (double-float) up strings per block x three block
+# sizes
+NV = 16
+KERNELS = [2] * 5 + [3] * 5 + [4] * 6
+
+
+def applicable(m, prec):
+    """Variants that apply to a sector of model m in format prec (all of these
+    cases have the fast tables)."""
+    if prec == "fp64":
+        return set(range(5))
+    moves = m.n_orb >= 2 and (m.Jsf != 0.0 or m.Jph != 0.0)
+    nat = not moves or m.orb0 + m.n_orb == m.n_s
+    if prec == "fp32":
+        return set(range(10, 16)) if nat else set(range(10))
+    return set(range(16)) if nat else set(range(10))
+
+
+def family(v):
+    return 0 if v < 5 else (1 if v < 10 else 2)
 
 CASES = [("Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6),
          ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7),
@@ -46,20 +68,28 @@ def test_variants_agree_bitwise_and_tuner_picks_fastest(env, name, mk, nu, nd, p
         xd = to_dev(x, prec, ed, torch)
         outs = {}
         nv = NV
+        app = applicable(m, prec)
         for v in range(nv):
             try:
                 ed.ed_sector_set_variant(sec, v)
             except ed.EdError:
-                assert prec == "fp64" and v >= nv // 2   # two-row variants exist for DF64 and FP32 only
+                assert v not in app, v
                 continue
+            assert v in app, v
             assert ed.ed_sector_get_variant(sec) == v
             y = empty_vec(dim, prec, ed, torch)
             ed.ed_apply_h(sec, xd, y)
             torch.cuda.synchronize()
             outs[v] = y
-        base = outs[0]
+        # bit for bit within a kernel family; double-float families sum in
+        # different orders, within the format's rounding
+        base = outs[min(app)]
         for v, y in outs.items():
-            assert torch.equal(y, base), (v, name, prec)
+            first = outs[min(u for u in outs if family(u) == family(v))]
+            assert torch.equal(y, first), (v, name, prec)
+            if family(v) != family(min(app)):
+                yb, bb = to_host(y, prec, dim, ed, torch), to_host(base, prec, dim, ed, torch)
+                assert rel_err(yb, bb) <= 1e-13, (v, rel_err(yb, bb))
         rows = np.unique(np.random.default_rng(1).integers(0, dim, 800))
         xin = x.astype(np.float32).astype(np.float64) if prec == "fp32" else x
         ref = osec.apply_rows(m, nu, nd, rows, xin)
@@ -70,13 +100,12 @@ def test_variants_agree_bitwise_and_tuner_picks_fastest(env, name, mk, nu, nd, p
         assert r.n_candidates == nv
         ms = np.array(r.ms[:nv])
         fit = ms > 0
-        assert fit[:nv // 2].any()
-        if prec == "fp64":
-            assert not fit[nv // 2:].any()
+        assert fit[min(app)]
+        assert all(v in app for v in np.nonzero(fit)[0])
         assert r.chosen == int(np.argmin(np.where(fit, ms, np.inf)))
         assert ed.ed_sector_get_variant(sec) == r.chosen
         assert ed.ed_sector_get_info(sec).kernel == r.kernel[r.chosen]
-        assert [r.kernel[i] for i in range(nv)] == [2] * (nv // 2) + [3] * (nv // 2)
+        assert [r.kernel[i] for i in range(nv)] == KERNELS
     finally:
         ed.ed_sector_destroy(sec)
 
@@ -139,7 +168,7 @@ def test_nothing_to_tune_and_bad_variants(env):
         ed.ed_sector_destroy(g)
     s = ed.ed_sector_create(ctx, m, 6, 6, "fp64")
     try:
-        for bad in (NV // 2, NV, -2, 100):
+        for bad in (5, 10, NV, -2, 100):
             with pytest.raises(ed.EdError):
                 ed.ed_sector_set_variant(s, bad)
         ed.ed_sector_set_variant(s, -1)
