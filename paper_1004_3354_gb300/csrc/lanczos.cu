@@ -233,6 +233,12 @@ int lanczos3_impl(Sector* s, const ed_lanczos_opts* o, double* evals, void* evec
       ED_TRY(R.regen(jj));
     }
     ED_LAUNCH_CHECK();
+    // unit norm (a ghost copy of a converged value leaves sum_j S_j v_j unnormalised)
+    for (int i = 0; i < kc; ++i) {
+      ED_TRY(dot_to(W, (const V*)(out + (size_t)i * n), (const V*)(out + (size_t)i * n), OP_NORM_INV, 0));
+      k_rescale<V><<<vgrid, 256, 0, st>>>(out + (size_t)i * n, n, c, 0);
+    }
+    ED_LAUNCH_CHECK();
   }
   ED_TRY_CUDA(cudaStreamSynchronize(st));
   if (info) {

@@ -383,6 +383,20 @@ __global__ void k_scale(const V* __restrict__ w, V* __restrict__ out, uint64_t n
   }
 }
 
+// v *= 1 / ||v|| (inv_d[slot] from OP_NORM_INV), in place.  Ritz vectors
+// regenerated from a three-vector recurrence need it: once a converged Ritz
+// value has a ghost copy (loss of orthogonality in finite precision, early
+// with float vectors) sum_j S_j v_j keeps its direction but not unit norm.
+template <class V>
+__global__ void k_rescale(V* __restrict__ v, uint64_t n, Coefs c, int slot) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    typename AccOf<V>::T a{};
+    amac(a, c.inv_d, c.inv_f, slot, v[i]);
+    v[i] = store_v(a, v);
+  }
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z += 0x9e3779b97f4a7c15ull;
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;

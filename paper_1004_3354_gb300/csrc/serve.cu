@@ -449,6 +449,13 @@ struct Server : ServerBase {
       ++q->vec_step;
     }
     if (q->vec_step < q->m_final) return ED_OK;
+    // unit norm: a ghost copy of the converged ground state (loss of
+    // orthogonality, early with float vectors) leaves sum_j S_j v_j unnormalised
+    k_dot<V><<<r->sgrid, kRedThreads, 0, q->st>>>(q->psi, q->psi, n, r->partial);
+    k_finish<<<1, kRedThreads, 0, q->st>>>(r->partial, (int)r->sgrid, OP_NORM_INV, 0, r->c, 0.0);
+    k_rescale<V><<<vg, 256, 0, q->st>>>(q->psi, n, r->c, 0);
+    ED_LAUNCH_CHECK();
+    ED_TRY_CUDA(cudaStreamSynchronize(q->st));  // r->c is freed with the ground-state run
     q->gs.reset();  // ground-state buffers are no longer needed
     ED_TRY(q->alloc(&q->dG, o.n_w));
     ED_TRY(q->alloc(&q->dE, 1));

@@ -42,12 +42,28 @@ def request_set():
     return reqs
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64"])
+# Tolerances against the oracle per vector format: ground energy (relative) and
+# max |G - G_oracle| over the Matsubara points.  FP64 and DF64 carry the
+# spec bounds (eigenvalues 1e-10, G 1e-8).  FP32 vectors round every stored
+# element to 2^-24 relative, so the ground energy is held to the 1e-6 relative
+# target for the FP32-vector form; G is built from float vectors (phi = c+ psi
+# and the Lanczos vectors of the continued fraction), whose coefficients carry
+# errors of a few 1e-7 relative, and |G| <= 1/w_0 = beta/pi ~ 12.7 here: 2e-5.
+SERVE_TOL = {"fp64": (1e-10, 1e-8), "df64": (1e-10, 1e-8), "fp32": (1e-6, 2e-5)}
+# Lanczos residual tolerance of the server per format: the three-vector
+# recurrence on float vectors loses orthogonality early and its residual
+# estimate does not reach 1e-11; 1e-7 still gives eigenvalues to ~1e-13 (the
+# eigenvalue error is quadratic in the residual).
+LZ_TOL = {"fp64": 1e-11, "df64": 1e-11, "fp32": 1e-7}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
 def test_server_results_match_oracle_and_are_mix_invariant(env, prec):
     ed, ctx, torch = env
     beta, nw, depth = 40.0, 256, 60
+    e_tol, g_tol = SERVE_TOL[prec]
     reqs = request_set()
-    srv = ed.ed_server_create(ctx, max_active=4, prec=prec, tol=1e-11, max_iter=400, cf_depth=depth, n_w=nw,
+    srv = ed.ed_server_create(ctx, max_active=4, prec=prec, tol=LZ_TOL[prec], max_iter=400, cf_depth=depth, n_w=nw,
                               beta=beta)
     try:
         # request 0 alone
@@ -68,9 +84,9 @@ def test_server_results_match_oracle_and_are_mix_invariant(env, prec):
             assert st == 0
             H = osec.build_csr(m, nu, nd)
             w, v = spectrum.lowest(H, 1, vectors=True)
-            assert abs(E0 - w[0]) <= 1e-10 * abs(w[0]), (m.n_s, E0, w[0])
+            assert abs(E0 - w[0]) <= e_tol * abs(w[0]), (m.n_s, E0, w[0])
             Gref = og.greens_cf(m, [(nu, nd, w[0], v[:, 0])], beta, nw, m.orb0, 0, depth=depth)
-            assert np.max(np.abs(G - Gref)) <= 1e-8, (m.n_s, np.max(np.abs(G - Gref)))
+            assert np.max(np.abs(G - Gref)) <= g_tol, (m.n_s, np.max(np.abs(G - Gref)))
         stats = ed.ed_server_get_stats(srv)
         assert stats.max_active_seen >= 2          # requests overlapped on the device
         assert stats.failed == 0
