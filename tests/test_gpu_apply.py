@@ -122,16 +122,14 @@ SAMPLED = [
 
 
 def fast_kernel(kern, prec, m=None):
-    """Kernel id ed_sector_get_info reports: float and double-float sectors on
-    the fast path run the natural-order kernel (4); where spin-flip / pair-hop
-    moves exist with the impurity orbitals off the top sites, float sectors run
-    the two-row kernel (3) and double-float ones the one-row kernel (2)."""
-    if kern != 2 or prec == "fp64":
+    """Kernel id ed_sector_get_info reports by default: float sectors on the
+    fast path run the natural-order kernel (4), or the two-row kernel (3) where
+    spin-flip / pair-hop moves exist with the impurity orbitals off the top
+    sites; FP64 and double-float sectors the one-row window kernel (2)."""
+    if kern != 2 or prec != "fp32":
         return kern
     moves = m is not None and m.n_orb >= 2 and (m.Jsf != 0.0 or m.Jph != 0.0)
-    if moves and m.orb0 + m.n_orb != m.n_s:
-        return 3 if prec == "fp32" else 2
-    return 4
+    return 3 if moves and m.orb0 + m.n_orb != m.n_s else 4
 
 
 @pytest.mark.parametrize("generic", [False, True], ids=["default", "generic"])

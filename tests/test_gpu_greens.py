@@ -175,7 +175,7 @@ def test_fast_kernel_sectors(env, prec):
     m = W.aim(12, seed=3)
     for nu, nd in ((7, 6), (5, 6)):
         s = ed.ed_sector_create(ctx, m, nu, nd, prec)
-        assert ed.ed_sector_get_info(s).kernel == (2 if prec == "fp64" else 4)   # a fast row kernel
+        assert ed.ed_sector_get_info(s).kernel == 2
         ed.ed_sector_destroy(s)
     sec = ed.ed_sector_create(ctx, m, 6, 6, "fp64")
     try:
