@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define ED_ABI_VERSION 1
+#define ED_ABI_VERSION 2
 
 typedef enum ed_status {
   ED_OK = 0,
@@ -428,24 +428,32 @@ int ed_batch_autotune(ed_batch* b, int steps, ed_batch_tune_result* out, void* s
 /* ---------------------------------------------------------------- serving */
 /* A request server for impurity solves, the work of one DMFT iteration (Sec. 2:
  * each iteration diagonalises a new impurity Hamiltonian and forms G(i w_n) of
- * Eq. 3).  A server thread admits queued requests while their estimated device
- * footprint fits the budget and a slot is free, and advances every admitted
- * request a few Lanczos steps per pass on its own stream (continuous batching:
- * requests join and leave between steps, their kernels overlap on the GPU).
- * Per request: ground state of the sector by three-vector Lanczos, its Ritz
- * vector, then (want_G) the particle and hole continued fractions of
- * c+_{orbital,spin} at depth cf_depth and G on n_w Matsubara points at beta.
+ * Eq. 3; Sec. 4 keeps the lowest states above a Boltzmann cutoff).  A server
+ * thread admits queued requests while their estimated device footprint fits
+ * the budget and a slot is free; admitted requests run concurrently, each on
+ * its own stream with its own scratch (continuous batching: requests join and
+ * leave as others finish, their kernels overlap on the GPU).
+ *  k = 1: ground state by three-vector Lanczos, advanced a few steps per server
+ *         pass (replays of captured step graphs), its Ritz vector, then (want_G)
+ *         the particle and hole continued fractions of c+_{orbital,spin} at
+ *         depth cf_depth and G on n_w Matsubara points at beta.
+ *  k > 1: the k lowest states of the sector by thick-restart Lanczos (basis of
+ *         max(4k + 8, 20) vectors, at most 64), run by a worker thread of the
+ *         server, then (want_G) G from those states with Boltzmann weights at
+ *         beta (states below a weight of 1e-5 relative to the lowest skipped),
+ *         as ed_greens_cf.
  * A request's kernels touch only its own buffers, so its result is bitwise the
  * same alone or in a mix.  The server's context must not be used from other
  * threads while the server runs. */
+#define ED_SERVE_MAX_K 16
 typedef struct ed_server ed_server;
 
 typedef struct ed_server_opts {
   size_t hbm_budget;   /* device bytes the admitted requests may hold together (0 = no limit) */
   int max_active;      /* requests on the GPU at once */
   int prec;            /* vector format of every request */
-  double tol;          /* ground-state residual tolerance (relative, as ed_lanczos) */
-  int max_iter;        /* ground-state Lanczos steps at most */
+  double tol;          /* residual tolerance of the eigensolve (relative, as ed_lanczos) */
+  int max_iter;        /* Lanczos steps (k = 1) or H*v products (k > 1, thick restart) at most */
   int cf_depth;        /* continued-fraction depth (1..1000) */
   int n_w;             /* Matsubara frequencies */
   double beta;         /* inverse temperature */
@@ -454,18 +462,21 @@ typedef struct ed_server_opts {
 
 typedef struct ed_request {
   const ed_model* model;  /* copied at submission */
-  int n_up, n_dn;         /* sector of the ground state */
+  int n_up, n_dn;         /* sector of the states */
   int want_G;             /* also compute G(i w_n) */
   int orbital, spin;      /* operator c+ of the Green's function */
+  int k;                  /* lowest states wanted, 1..ED_SERVE_MAX_K (0 means 1) */
 } ed_request;
 
 typedef struct ed_result {
   int status;          /* ED_OK, ED_ERR_NOT_CONVERGED or the failure */
   double E0;           /* ground energy of the sector */
-  int iters;           /* ground-state Lanczos steps */
+  int iters;           /* Lanczos steps (H*v products) of the eigensolve */
   double latency_ms;   /* submission to completion */
   double queue_ms;     /* submission to admission */
   int n_w;             /* G entries written (0 without want_G) */
+  int n_E;             /* energies in E (k, or the sector dimension if smaller) */
+  double E[ED_SERVE_MAX_K];  /* lowest energies, ascending */
 } ed_result;
 
 typedef struct ed_server_stats {
@@ -478,7 +489,7 @@ int ed_server_create(ed_ctx* ctx, const ed_server_opts* opts, ed_server** out);
 /* Stop the thread and free everything (unpolled results are dropped). */
 int ed_server_destroy(ed_server* s);
 /* Queue a request; never blocks on the GPU.  ED_ERR_OOM if the request alone
- * exceeds the whole budget, ED_ERR_INVALID for a bad model or sector. */
+ * exceeds the whole budget, ED_ERR_INVALID for a bad model, sector or k. */
 int ed_submit(ed_server* s, const ed_request* req, uint64_t* ticket);
 /* Non-blocking: *done = 1 and the result (and G, 2*n_w doubles re/im, if
  * non-NULL) once the request has finished; the ticket is then released.

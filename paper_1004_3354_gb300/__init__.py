@@ -95,14 +95,18 @@ class ed_server_opts(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+ED_SERVE_MAX_K = 16
+ABI_VERSION = 2   # ED_ABI_VERSION of include/ed.h that these structures follow
+
+
 class ed_request(C.Structure):
     _fields_ = [("model", C.POINTER(ed_model)), ("n_up", C.c_int), ("n_dn", C.c_int), ("want_G", C.c_int),
-                ("orbital", C.c_int), ("spin", C.c_int)]
+                ("orbital", C.c_int), ("spin", C.c_int), ("k", C.c_int)]
 
 
 class ed_result(C.Structure):
     _fields_ = [("status", C.c_int), ("E0", C.c_double), ("iters", C.c_int), ("latency_ms", C.c_double),
-                ("queue_ms", C.c_double), ("n_w", C.c_int)]
+                ("queue_ms", C.c_double), ("n_w", C.c_int), ("n_E", C.c_int), ("E", C.c_double * ED_SERVE_MAX_K)]
 
 
 class ed_server_stats(C.Structure):
@@ -182,6 +186,9 @@ def lib():
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
+        if L.ed_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"{LIB_PATH} has ABI version {L.ed_abi_version()}, this binding expects "
+                               f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
         _lib = L
     return _lib
 
@@ -503,10 +510,10 @@ def ed_server_destroy(srv):
     return check(lib().ed_server_destroy(srv))
 
 
-def ed_submit(srv, model, n_up, n_dn, want_G=True, orbital=None, spin=ED_SPIN_UP) -> int:
+def ed_submit(srv, model, n_up, n_dn, want_G=True, orbital=None, spin=ED_SPIN_UP, k=1) -> int:
     mm = model if isinstance(model, Model) else Model(model)
     orb = int(getattr(mm.src, "orb0", 0)) if orbital is None else int(orbital)
-    r = ed_request(C.pointer(mm.c), int(n_up), int(n_dn), 1 if want_G else 0, orb, int(spin))
+    r = ed_request(C.pointer(mm.c), int(n_up), int(n_dn), 1 if want_G else 0, orb, int(spin), int(k))
     t = C.c_uint64()
     check(lib().ed_submit(srv, C.byref(r), C.byref(t)))
     return t.value

@@ -34,6 +34,7 @@ void set_error(const char* fmt, ...) {
 
 int dev_alloc(Ctx* c, void** p, size_t bytes) {
   *p = nullptr;
+  c = ctx_root(c);
   if (bytes == 0) bytes = 1;
   if (c->budget && c->in_use + bytes > c->budget) {
     set_error("HBM budget exceeded: %zu in use + %zu requested > %zu", c->in_use.load(), bytes, c->budget);
@@ -55,11 +56,38 @@ int dev_alloc(Ctx* c, void** p, size_t bytes) {
 
 void dev_free(Ctx* c, void* p, size_t bytes) {
   if (!p) return;
+  c = ctx_root(c);
   cudaFree(p);
   if (bytes == 0) bytes = 1;
   size_t cur = c->in_use.load();
   while (!c->in_use.compare_exchange_weak(cur, cur - std::min(cur, bytes))) {
   }
+}
+
+int make_sub_ctx(Ctx* parent, Ctx* sub) {
+  Ctx* r = ctx_root(parent);
+  sub->root = r;
+  sub->device = r->device;
+  sub->device_name = r->device_name;
+  sub->num_sms = r->num_sms;
+  sub->smem_optin = r->smem_optin;
+  sub->smem_per_sm = r->smem_per_sm;
+  sub->d_binom = r->d_binom;  // read-only, owned by the root
+  ED_TRY(dev_alloc_n(sub, &sub->d_red, kRedSlots));
+  if (cudaMallocHost(&sub->h_red, 4096) != cudaSuccess) {
+    dev_free(sub, sub->d_red, kRedSlots * sizeof(double));
+    sub->d_red = nullptr;
+    set_error("cudaMallocHost failed");
+    return ED_ERR_OOM;
+  }
+  return ED_OK;
+}
+
+void free_sub_ctx(Ctx* sub) {
+  dev_free(sub, sub->d_red, kRedSlots * sizeof(double));
+  sub->d_red = nullptr;
+  if (sub->h_red) cudaFreeHost(sub->h_red);
+  sub->h_red = nullptr;
 }
 
 int convert_async(const void* src, int sp, void* dst, int dp, uint64_t n, cudaStream_t st);

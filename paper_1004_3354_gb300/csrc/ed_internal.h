@@ -58,7 +58,17 @@ struct Ctx {
   uint32_t* d_binom = nullptr;   // [33][33] binomial coefficients C(n, k)
   double* d_red = nullptr;       // reduction scratch (partials), kRedSlots doubles
   double* h_red = nullptr;       // pinned host mirror of d_red[0..63]
+  // A sub-context (a worker thread of the request server) has its own
+  // reduction scratch and charges its allocations to, and shares the autotune
+  // cache of, the context it was made from.
+  Ctx* root = nullptr;
 };
+
+inline Ctx* ctx_root(Ctx* c) { return c->root ? c->root : c; }
+// Make sub a sub-context of parent (own reduction scratch, parent's budget,
+// device tables and autotune cache); free_sub_ctx releases its scratch.
+int make_sub_ctx(Ctx* parent, Ctx* sub);
+void free_sub_ctx(Ctx* sub);
 
 constexpr int kRedSlots = 8192;
 

@@ -31,6 +31,11 @@
 
 namespace ed {
 
+int trlan_run(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed_trlan_info* info,
+              cudaStream_t st);
+int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
+                  int n_w, const double* z, int orbital, int spin, int depth, double boltz_cut, double* G,
+                  double* coeffs, cudaStream_t st);
 int greens_accumulate(double2* dG, int n_w, double beta, const double* da, const double* db, int L, double n2,
                       const double* dE, int n_states, int nu, int sgn, cudaStream_t st);
 
@@ -152,14 +157,18 @@ struct Run3 {
   }
 };
 
-enum Phase { PH_QUEUED = 0, PH_GS, PH_GS_CHECK, PH_VEC, PH_CF, PH_CF_WAIT, PH_EVAL_WAIT, PH_DONE, PH_FAILED };
+enum Phase { PH_QUEUED = 0, PH_GS, PH_GS_CHECK, PH_VEC, PH_CF, PH_CF_WAIT, PH_EVAL_WAIT, PH_WORK, PH_DONE,
+             PH_FAILED };
+
+// Thick-restart basis of a k > 1 request: max(4k + 8, 20) vectors, at most 64.
+inline int tr_basis(int k) { return std::min(std::max(4 * k + 8, 20), 64); }
 
 template <class V>
 struct Req {
   uint64_t ticket = 0;
   std::vector<double> T, U;
   ed_model model{};
-  int n_up = 0, n_dn = 0, want_G = 1, orbital = 0, spin = 0;
+  int n_up = 0, n_dn = 0, want_G = 1, orbital = 0, spin = 0, k = 1;
   Phase phase = PH_QUEUED;
   size_t footprint = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -191,6 +200,11 @@ struct Req {
   double* dE = nullptr;
   double* dab = nullptr;
   std::vector<double> G;
+  std::vector<double> Ek;   // lowest energies (k > 1, or E0 alone)
+  // k > 1: worker thread with its own sub-context (private reduction scratch)
+  std::thread worker;
+  std::atomic<bool> wdone{false};
+  std::unique_ptr<Ctx> sub;
   std::vector<std::pair<void*, size_t>> allocs;
   Ctx* ctx = nullptr;
   template <class T>
@@ -200,6 +214,7 @@ struct Req {
     return r;
   }
   void release() {
+    if (worker.joinable()) worker.join();
     gs.reset();
     cf.reset();
     if (sec) free_sector(sec.get());
@@ -208,6 +223,8 @@ struct Req {
     sec_cf.reset();
     for (auto& a : allocs) dev_free(ctx, a.first, a.second);
     allocs.clear();
+    if (sub) free_sub_ctx(sub.get());
+    sub.reset();
     if (h_pin) cudaFreeHost(h_pin);
     h_pin = nullptr;
     if (ev) cudaEventDestroy(ev);
@@ -249,12 +266,13 @@ struct Server : ServerBase {
     stop = true;
     cv.notify_all();
     if (th.joinable()) th.join();
+    // workers of k > 1 requests run to the end of their solve (release joins them)
     cudaSetDevice(ctx->device);
     for (auto& r : active) r->release();
     for (auto& kv : finished) kv.second->release();
   }
 
-  size_t estimate(int n_s, int nu, int nd) const {
+  size_t estimate(int n_s, int nu, int nd, int k) const {
     auto C = [](int n, int k) -> double {
       if (k < 0 || k > n) return 0;
       double r = 1;
@@ -262,8 +280,16 @@ struct Server : ServerBase {
       return r;
     };
     const double dim = C(n_s, nu) * C(n_s, nd);
-    const double dcf = std::max(C(n_s, nu + 1) * C(n_s, nd), C(n_s, nu - 1) * C(n_s, nd));
+    const double dcf = std::max({C(n_s, nu + 1) * C(n_s, nd), C(n_s, nu - 1) * C(n_s, nd),
+                                 C(n_s, nu) * C(n_s, nd + 1), C(n_s, nu) * C(n_s, nd - 1)});
     const double eb = (double)elem_bytes(o.prec);
+    if (k > 1) {
+      // thick-restart basis (m + 2 + keep slots, padded) and the k Ritz vectors,
+      // then the Green's function: both neighbour sectors' tables, phi and the
+      // four vectors of the coefficient recurrence, plus tables
+      const double m = tr_basis(k), keep = (m + k) / 2.0;
+      return (size_t)(((m + 2.0 + keep + k) * (dim + 32.0) + 6.0 * dcf) * eb + 96.0 * 1024 * 1024);
+    }
     // ground-state run (5 vectors) + psi, then CF run (5 vectors) + phi, tables
     return (size_t)((6.0 * dim + 6.0 * dcf) * eb + 64.0 * 1024 * 1024);
   }
@@ -283,8 +309,10 @@ struct Server : ServerBase {
     q->want_G = r->want_G;
     q->orbital = r->orbital;
     q->spin = r->spin;
+    q->k = r->k < 1 ? 1 : r->k;
+    if (q->k > ED_SERVE_MAX_K) ED_INVALID("k = %d outside 1..%d", r->k, ED_SERVE_MAX_K);
     q->ctx = ctx;
-    q->footprint = estimate(m->n_s, r->n_up, r->n_dn);
+    q->footprint = estimate(m->n_s, r->n_up, r->n_dn, q->k);
     if (o.hbm_budget && q->footprint > o.hbm_budget) {
       set_error("request needs ~%zu bytes, more than the whole server budget %zu", q->footprint, o.hbm_budget);
       return ED_ERR_OOM;
@@ -316,6 +344,9 @@ struct Server : ServerBase {
       res->latency_ms = q->t_done - q->t_submit;
       res->queue_ms = q->t_admit - q->t_submit;
       res->n_w = q->want_G ? o.n_w : 0;
+      const std::vector<double>& E = q->Ek.empty() ? std::vector<double>(1, q->E0) : q->Ek;
+      res->n_E = (int)std::min<size_t>(E.size(), ED_SERVE_MAX_K);
+      for (int i = 0; i < ED_SERVE_MAX_K; ++i) res->E[i] = i < res->n_E ? E[i] : NAN;
     }
     if (G && q->want_G && !q->G.empty()) std::memcpy(G, q->G.data(), sizeof(double) * q->G.size());
     int st = q->status;
@@ -344,11 +375,74 @@ struct Server : ServerBase {
     q->phase = PH_FAILED;
   }
 
+  // ---- k > 1: the whole solve on a worker thread, on the request's stream,
+  // with a sub-context of its own (private reduction scratch)
+  int solve_k(Req<V>* q) {
+    ED_TRY_CUDA(cudaSetDevice(ctx->device));
+    q->sub.reset(new Ctx());
+    ED_TRY(make_sub_ctx(ctx, q->sub.get()));
+    q->sec.reset(new Sector());
+    ED_TRY(build_sector(q->sub.get(), &q->model, q->n_up, q->n_dn, o.prec, q->sec.get()));
+    ED_TRY(build_fast(q->sec.get()));
+    const uint64_t n = q->sec->dim;
+    const int kk = (int)std::min<uint64_t>((uint64_t)q->k, n);
+    ed_trlan_opts to{};
+    to.k = kk;
+    to.tol = o.tol;
+    to.max_basis = (int)std::min<uint64_t>((uint64_t)tr_basis(q->k), n);
+    to.keep = 0;
+    to.max_iter = o.max_iter;
+    to.check_every = 4;
+    to.seed = o.seed;
+    to.v0 = nullptr;
+    V* evecs = nullptr;
+    ED_TRY(q->alloc(&evecs, (size_t)kk * n));
+    std::vector<double> ev(std::max(kk, 1));
+    ed_trlan_info info{};
+    const int st = trlan_run(q->sec.get(), &to, ev.data(), evecs, &info, q->st);
+    if (st != ED_OK && st != ED_ERR_NOT_CONVERGED) return st;
+    q->Ek.assign(ev.begin(), ev.begin() + kk);
+    q->E0 = ev[0];
+    q->gs_iters = info.iters;
+    if (q->want_G) {
+      std::vector<ed_state> states(kk);
+      for (int i = 0; i < kk; ++i) states[i] = ed_state{q->n_up, q->n_dn, ev[i], evecs + (size_t)i * n};
+      q->G.assign(2 * (size_t)o.n_w, 0.0);
+      ED_TRY(greens_cf_run(q->sub.get(), &q->model, o.prec, kk, states.data(), o.beta, o.n_w, nullptr, q->orbital,
+                           q->spin, o.cf_depth, 1e-5, q->G.data(), nullptr, q->st));
+    }
+    ED_TRY_CUDA(cudaStreamSynchronize(q->st));
+    return st;
+  }
+
+  void run_worker(Req<V>* q) {
+    const int st = solve_k(q);
+    if (st != ED_OK) {
+      char buf[512];
+      ed_last_error(buf, sizeof(buf));  // this thread's message
+      q->status = st;
+      q->err = st == ED_ERR_NOT_CONVERGED ? "thick-restart Lanczos did not converge within max_iter" : buf;
+    }
+    q->wdone = true;
+  }
+
+  int check_work(Req<V>* q) {
+    if (!q->wdone) return ED_OK;
+    q->worker.join();
+    q->phase = (q->status == ED_OK || q->status == ED_ERR_NOT_CONVERGED) ? PH_DONE : PH_FAILED;
+    return ED_OK;
+  }
+
   // ---- per-request work, one call per server pass
   int admit(Req<V>* q) {
     cudaSetDevice(ctx->device);
     ED_TRY_CUDA(cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking));
     ED_TRY_CUDA(cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming));
+    if (q->k > 1) {
+      q->phase = PH_WORK;
+      q->worker = std::thread([this, q] { run_worker(q); });
+      return ED_OK;
+    }
     ED_TRY_CUDA(cudaMallocHost(&q->h_pin, sizeof(double) * 4096));
     q->sec.reset(new Sector());
     ED_TRY(build_sector(ctx, &q->model, q->n_up, q->n_dn, o.prec, q->sec.get()));
@@ -560,6 +654,7 @@ struct Server : ServerBase {
       case PH_CF: return step_cf(q);
       case PH_CF_WAIT: return finish_cf(q);
       case PH_EVAL_WAIT: return check_eval(q);
+      case PH_WORK: return check_work(q);
       default: return ED_OK;
     }
   }

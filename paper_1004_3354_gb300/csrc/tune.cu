@@ -50,6 +50,7 @@ std::string tune_key(const Sector* s) {
 void tune_apply_cached(Sector* s) {
   if (!s->fast.ok) return;
   Ctx* c = s->ctx;
+  c = ctx_root(c);
   std::lock_guard<std::mutex> lk(c->tune_mu);
   auto it = c->tune_cache.find(tune_key(s));
   if (it != c->tune_cache.end() && fast_variant_applies(s, it->second)) s->tune = it->second;
@@ -115,8 +116,9 @@ int autotune(Sector* s, int reps, ed_tune_result* out, cudaStream_t st) {
   set_error("");
   if (out->chosen >= 0) {
     s->tune = out->chosen;  // candidate i is variant i
-    std::lock_guard<std::mutex> lk(s->ctx->tune_mu);
-    s->ctx->tune_cache[tune_key(s)] = s->tune;
+    Ctx* r = ctx_root(s->ctx);
+    std::lock_guard<std::mutex> lk(r->tune_mu);
+    r->tune_cache[tune_key(s)] = s->tune;
   }
   return ED_OK;
 }

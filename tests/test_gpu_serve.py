@@ -21,6 +21,9 @@ def env():
     ed.ed_ctx_destroy(ctx)
 
 
+_poll_energies = {}   # ticket -> (status, ed_result, G) as polled
+
+
 def wait_all(ed, srv, tickets, timeout=300.0):
     out, t0 = {}, time.time()
     while len(out) < len(tickets):
@@ -30,6 +33,7 @@ def wait_all(ed, srv, tickets, timeout=300.0):
             done, res, G = ed.ed_poll(srv, t)
             if done:
                 out[t] = (res.status, res.E0, res.iters, G, res.latency_ms)
+                _poll_energies[t] = (res.status, res, G)
         assert time.time() - t0 < timeout, "server did not finish in time"
         time.sleep(0.002)
     return out
@@ -123,5 +127,44 @@ def test_server_admission_budget_and_errors(env):
             ed.ed_poll(srv, ts[0])
         with pytest.raises(ed.EdError):
             ed.ed_poll(srv, 10 ** 9)
+    finally:
+        ed.ed_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_server_k_lowest_states_match_oracle_and_are_mix_invariant(env, prec):
+    """k = 4 lowest states per request (thick restart on a server worker thread)
+    and G from all four with Boltzmann weights at beta = 40 (Sec. 4 keeps the
+    states above a 1e-5 weight): energies and G against the oracle, and the
+    same request alone and in a mix of k = 1 and k = 4 requests, bit for bit."""
+    ed, ctx, torch = env
+    beta, nw, depth, k = 40.0, 128, 50, 4
+    e_tol, g_tol = SERVE_TOL[prec]
+    reqs = request_set()[:5]
+    srv = ed.ed_server_create(ctx, max_active=4, prec=prec, tol=LZ_TOL[prec], max_iter=3000, cf_depth=depth,
+                              n_w=nw, beta=beta)
+    try:
+        m0, nu0, nd0 = reqs[2]
+        t_alone = ed.ed_submit(srv, m0, nu0, nd0, k=k)
+        alone = wait_all(ed, srv, [t_alone])
+        ts = [ed.ed_submit(srv, m, nu, nd, k=(k if i % 2 == 0 else 1)) for i, (m, nu, nd) in enumerate(reqs)]
+        res = wait_all(ed, srv, ts)
+        mix = res[ts[2]]
+        assert alone[t_alone][0] == 0 and mix[0] == 0
+        assert alone[t_alone][1] == mix[1]
+        assert np.array_equal(alone[t_alone][3], mix[3])
+        for i, ((m, nu, nd), t) in enumerate(zip(reqs, ts)):
+            st, E0, iters, G, lat = res[t]
+            assert st == 0, (i, st)
+            _, r, _ = _poll_energies[t]
+            kk = k if i % 2 == 0 else 1
+            H = osec.build_csr(m, nu, nd)
+            w, v = spectrum.lowest(H, kk, vectors=True)
+            assert r.n_E == kk
+            E = np.array(r.E[:kk])
+            assert np.max(np.abs(E - w) / np.abs(w)) <= e_tol, (m.n_s, E, w)
+            Gref = og.greens_cf(m, [(nu, nd, w[j], v[:, j]) for j in range(kk)], beta, nw, m.orb0, 0, depth=depth)
+            assert np.max(np.abs(G - Gref)) <= g_tol, (m.n_s, np.max(np.abs(G - Gref)))
+        assert ed.ed_server_get_stats(srv).failed == 0
     finally:
         ed.ed_server_destroy(srv)
