@@ -179,6 +179,20 @@ int ed_sector_csr_rows(const ed_sector* s, uint64_t row0, uint64_t nrows,
  * `dim` elements in the sector's format; y is overwritten; x and y must not
  * overlap.  Stream-ordered, no synchronisation, no allocation. */
 int ed_apply_h(ed_sector* s, const void* x, void* y, void* stream);
+/* y = H x for n_vec vectors in HOST memory, end to end (the same matrix-free
+ * product as ed_apply_h, Sec. 3.2): x_host and y_host hold n_vec vectors of
+ * `dim` elements each in the sector's format, one after the other.  Every
+ * vector crosses the host link once each way; the copies run on internal
+ * streams, pipelined with the applies (the copy-in of vector i + 1 and the
+ * copy-out of vector i - 1 overlap H*v of vector i).  Pinned host memory
+ * (cudaHostAlloc, cudaHostRegister) gives the link's full rate; pageable memory
+ * works at a lower one.  The work is ordered after what is already queued on
+ * `stream`, and the call returns when y_host is complete (it synchronises
+ * `stream`).  The first call on a sector allocates four device vectors
+ * (against the context's budget) and three streams, kept until
+ * ed_sector_destroy; calls on one sector must not overlap.  ED_ERR_INVALID for
+ * NULL pointers, ED_ERR_OOM if the four vectors do not fit. */
+int ed_apply_h_host(ed_sector* s, uint64_t n_vec, const void* x_host, void* y_host, void* stream);
 /* y = H x from the stored CSR matrix (the Listing 1 product over Fig. 1's
  * arrays).  Needs ED_SECTOR_CSR and ED_PREC_FP64. */
 int ed_apply_h_csr(ed_sector* s, const void* x, void* y, void* stream);

@@ -134,6 +134,7 @@ _SIGS = {
     "ed_sector_hops": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_sector_csr_rows": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_apply_h": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ed_apply_h_host": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_apply_h_csr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ed_convert": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     "ed_dot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_double),
@@ -206,7 +207,10 @@ def check(status: int, allow=()):
 
 
 def _ptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Address of a torch tensor's or numpy array's data (None stays NULL)."""
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else t.ctypes.data)
 
 
 def _stream(stream):
@@ -299,6 +303,12 @@ def ed_sector_csr_rows(sec, row0: int, nrows: int):
 # ------------------------------------------------------------------ apply
 def ed_apply_h(sec, x, y, stream=None):
     return check(lib().ed_apply_h(sec, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ed_apply_h_host(sec, n_vec, x_host, y_host, stream=None):
+    """y = H x for n_vec host vectors (pinned torch tensors or numpy arrays,
+    n_vec * dim elements each in the sector's format); returns when y is complete."""
+    return check(lib().ed_apply_h_host(sec, int(n_vec), _ptr(x_host), _ptr(y_host), _stream(stream)))
 
 
 def ed_apply_h_csr(sec, x, y, stream=None):

@@ -13,6 +13,7 @@ struct ed_ctx {
 };
 struct ed_sector {
   ed::Sector s;
+  ed::HostXfer* xfer = nullptr;  // buffers of ed_apply_h_host, made at its first call
 };
 
 namespace ed {
@@ -266,6 +267,7 @@ int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn, int
 int ed_sector_destroy(ed_sector* s) {
   if (!s) return ED_OK;
   cudaSetDevice(s->s.ctx->device);
+  host_xfer_free(s->s.ctx, s->xfer);
   free_sector(&s->s);
   delete s;
   return ED_OK;
@@ -352,6 +354,11 @@ int ed_sector_csr_rows(const ed_sector* h, uint64_t row0, uint64_t nrows, uint64
 int ed_apply_h(ed_sector* h, const void* x, void* y, void* stream) {
   if (!h) ED_INVALID("NULL sector");
   return apply_h(&h->s, x, y, as_stream(stream));
+}
+
+int ed_apply_h_host(ed_sector* h, uint64_t n_vec, const void* x_host, void* y_host, void* stream) {
+  if (!h) ED_INVALID("NULL sector");
+  return apply_h_host(&h->s, &h->xfer, n_vec, x_host, y_host, as_stream(stream));
 }
 
 int ed_apply_h_csr(ed_sector* h, const void* x, void* y, void* stream) {

@@ -82,6 +82,32 @@ int dev_alloc_n(Ctx* c, T** p, size_t n) {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in maximum
+// before a launch that needs `need` bytes.  Every call sets the same value, so
+// host threads that launch one kernel with different sizes (server workers,
+// sectors of several sizes) cannot undo each other's setting between set and
+// launch; occupancy still follows each launch's own size.
+template <class K>
+int smem_cap(const Ctx* c, K kern, size_t need) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) {
+    set_error("cudaFuncGetAttributes failed: %s", cudaGetErrorString(e));
+    return ED_ERR_CUDA;
+  }
+  const size_t cap = c->smem_optin > fa.sharedSizeBytes ? c->smem_optin - fa.sharedSizeBytes : 0;  // per kernel
+  if (need > cap) {
+    set_error("kernel needs %zu bytes of dynamic shared memory, more than the %zu a block may have", need, cap);
+    return ED_ERR_INVALID;
+  }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+  if (e != cudaSuccess) {
+    set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
+    return ED_ERR_CUDA;
+  }
+  return ED_OK;
+}
+
 // The context behind an opaque handle (abi.cu).
 Ctx* ctx_of(ed_ctx* h);
 
@@ -254,6 +280,12 @@ bool fast_variant_applies(const Sector* s, int v);
 int fast_default_variant(const Sector* s);
 int apply_fast_variant(const Sector* s, int v, const void* x, void* y, cudaStream_t st, double* dotp = nullptr,
                        int* nparts = nullptr);
+
+// Host-buffer H*v (hostio.cu): pipelined copies and applies over n_vec vectors;
+// the device buffers and streams are made at the first call and kept in *hp.
+struct HostXfer;
+int apply_h_host(Sector* s, HostXfer** hp, uint64_t n_vec, const void* xh, void* yh, cudaStream_t st);
+void host_xfer_free(Ctx* c, HostXfer* h);
 
 // Apply entry points (apply.cu, csr.cu)
 int apply_h(const Sector* s, const void* x, void* y, cudaStream_t st);

@@ -236,3 +236,43 @@ def test_apply_is_deterministic_and_symmetric(env):
             ed.ed_apply_h(sec, a, a)
     finally:
         ed.ed_sector_destroy(sec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_apply_host_buffers_pipeline(env, prec):
+    """ed_apply_h_host: n_vec vectors from pinned host memory, copies pipelined
+    with the applies on internal streams, gives y bit for bit equal to
+    ed_apply_h on device copies of the same vectors, for n_vec = 3 (both
+    device buffers reused), 1 and 0, from pinned and from pageable memory."""
+    ed, ctx, torch = env
+    m = W.kanamori(12, seed=0)
+    sec = ed.ed_sector_create(ctx, m, 6, 5, prec)
+    try:
+        dim = ed.ed_sector_get_info(sec).dim
+        n_vec = 3
+        xs = [to_dev(W.random_vector(dim, seed=10 + i), prec, ed, torch) for i in range(n_vec)]
+        ref = []
+        for xd in xs:
+            yd = torch.empty_like(xd)
+            ed.ed_apply_h(sec, xd, yd)
+            ref.append(yd.cpu())
+        torch.cuda.synchronize()
+        hx = torch.cat([xd.cpu() for xd in xs]).pin_memory()
+        hy = torch.full_like(hx, float("nan")).pin_memory()
+        ed.ed_apply_h_host(sec, n_vec, hx, hy)
+        per = hx.numel() // n_vec
+        for i in range(n_vec):
+            assert torch.equal(hy[i * per:(i + 1) * per], ref[i]), i
+        hy1 = torch.full_like(hx[:per], float("nan")).pin_memory()
+        ed.ed_apply_h_host(sec, 1, hx[per:2 * per], hy1)
+        assert torch.equal(hy1, ref[1])
+        ed.ed_apply_h_host(sec, 0, hx, hy1)            # nothing to do
+        assert torch.equal(hy1, ref[1])
+        npx = hx[2 * per:].numpy().copy()               # pageable numpy buffers
+        npy = np.full_like(npx, np.nan)
+        ed.ed_apply_h_host(sec, 1, npx, npy)
+        assert np.array_equal(npy, ref[2].numpy())
+        with pytest.raises(ed.EdError):
+            ed.ed_apply_h_host(sec, 1, None, hy1)
+    finally:
+        ed.ed_sector_destroy(sec)
