@@ -811,7 +811,7 @@ int launch_fast(const Sector* s, const void* x, void* y, cudaStream_t st, double
   F.dotp = dotp;
   size_t smem = fast_smem<P>(F.D, F.n_coef, F.n_lp, F.lcap);
   auto kern = k_apply_win<P, BS, MINB>;
-  ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ED_TRY(smem_cap(s->ctx, kern, smem));
   int per_sm = 0;
   ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem));
   if (per_sm < 1) ED_INVALID("fast row kernel does not fit on an SM (%zu B shared)", smem);
@@ -830,7 +830,7 @@ int launch_pair(const Sector* s, const void* x, void* y, cudaStream_t st, double
   F.dotp = dotp;
   size_t smem = pair_smem<P>(F.D, F.n_coef);
   auto kern = k_apply_pair<P, BS, MINB>;
-  ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ED_TRY(smem_cap(s->ctx, kern, smem));
   int per_sm = 0;
   ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem));
   if (per_sm < 1) ED_INVALID("two-row kernel does not fit on an SM (%zu B shared)", smem);

@@ -479,7 +479,7 @@ int launch_nat_t(const Sector* s, const void* x, void* y, cudaStream_t st, doubl
   F.dotp = dotp;
   const size_t smem = nat_smem(R, sizeof(V), F.D, F.n_coef, F.n_pat, F.n_md, F.n_lp, F.lcap);
   auto kern = k_apply_nat<P, R, BS, MINB>;
-  ED_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ED_TRY(smem_cap(s->ctx, kern, smem));
   int per_sm = 0;
   ED_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BS, smem));
   if (per_sm < 1) ED_INVALID("natural-order kernel does not fit on an SM (%zu B shared)", smem);

@@ -168,7 +168,10 @@ __global__ void k_tr_keep(const double* __restrict__ theta, const double* __rest
 int jacobi(cudaStream_t st, const double* Hp, int m, int ld, double* theta, double* S, float2* Sf, int ldS,
            double* Y) {
   const size_t smem = (size_t)m * m * sizeof(double);
-  ED_TRY_CUDA(cudaFuncSetAttribute(k_sym_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // one cap for every size (kMaxBasis^2 doubles): concurrent solves of different
+  // basis sizes set the same value
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_sym_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)kMaxBasis * kMaxBasis * sizeof(double))));
   k_sym_jacobi<<<1, kJacThreads, smem, st>>>(Hp, m, ld, theta, S, Sf, ldS, Y, nullptr);
   ED_LAUNCH_CHECK();
   return ED_OK;
