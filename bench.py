@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "H*v GB/s (% of HBM peak) at N_s=15"
+METRIC = "H*v GB/s (% of HBM peak) at N_s=15; solves/s, p99 latency vs plain FP64"
 NS, NUP, NDN = 15, 7, 8
 SEED = 0
 
@@ -50,7 +50,7 @@ def args_parse(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--prec", default="df64", choices=["df64", "fp64", "fp32"])
-    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--e2e-steps", type=int, default=12)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 / FP32 side measurements")
     p.add_argument("--no-autotune", action="store_true", help="time the untuned default H*v variant")
@@ -60,6 +60,9 @@ def args_parse(argv=None):
                         "serve: Poisson stream of impurity solves, N_s in 10..16; "
                         "solve15: N_s=15 ground state + G(i w_n) per vector format, and the stored-CSR H*v")
     p.add_argument("--requests", type=int, default=40)
+    p.add_argument("--serve-requests", type=int, default=16, help="requests of the serve block in the default line")
+    p.add_argument("--serve-tol", type=float, default=1e-8)
+    p.add_argument("--no-serve", action="store_true", help="skip the serve block of the default line")
     return p.parse_args(argv)
 
 
@@ -74,11 +77,14 @@ def workload_config(prec, dim):
 
 # Arithmetic ceiling of one H*v.  Multiply-adds per element: the off-diagonal
 # entries of the row plus two for the diagonal (e_dn + W and e_up).  A
-# double-float multiply-add is 12 FP32 instructions (10 when x is a float);
-# FP64 rows take one DFMA.  Peaks from the unit counts at the 2.07 GHz maximum
-# SM clock: 152 SMs x 128 FP32 lanes; 152 SMs x 2 DFMA per clock.
+# double-float multiply-add is 12 FP32 instructions; float vectors take one FP32
+# FMA per multiply-add (natural-order kernel, float sums); FP64 rows take one
+# DFMA.  FP32 peak from the unit counts at the 2.07 GHz maximum SM clock (152
+# SMs x 128 FP32 lanes).  The FP64 peak is the measured DFMA rate on this GPU
+# (a dependent-FMA probe on every SM: 0.50 T DFMA/s, about 1.6 per SM per clock),
+# since GB300's FP64 pipe does not reach a unit-count figure.
 FP32_PEAK = 152 * 128 * 2.07e9
-DFMA_PEAK = 152 * 2 * 2.07e9
+DFMA_PEAK = 0.50e12
 
 
 def alu_roofline(prec, dim, nnz_per_row, launch_ms):
@@ -86,11 +92,12 @@ def alu_roofline(prec, dim, nnz_per_row, launch_ms):
     if prec == "fp64":
         ops, peak, unit = macs, DFMA_PEAK, "T DFMA/s"
     else:
-        ops, peak, unit = macs * (12 if prec == "df64" else 10), FP32_PEAK, "T FP32 instructions/s"
+        ops, peak, unit = macs * (12 if prec == "df64" else 1), FP32_PEAK, "T FP32 instructions/s"
     achieved = ops / (launch_ms * 1e-3)
     return {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak / 1e12, 3), "unit": unit,
             "frac": round(achieved / peak, 4), "ops_per_launch": ops, "macs_per_element": nnz_per_row + 1.0,
-            "peak_source": "unit counts x 2.07 GHz maximum SM clock"}
+            "peak_source": ("measured DFMA rate (probe)" if prec == "fp64"
+                            else "unit counts x 2.07 GHz maximum SM clock")}
 
 
 def ranks_max(vals, dist, device):
@@ -181,24 +188,126 @@ def oracle_rows_rate(model, x, seconds, rng):
             return done / el, done, el
 
 
-def cpu_baseline(model, x, prec, seconds):
-    rng = np.random.default_rng(123)
-    rate, done, el = oracle_rows_rate(model, x, seconds, rng)
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":", 1)[0].strip().lower()
+            if k in ("model name", "cpu part", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_csr_block(model, n_up, n_dn, row0, nrows):
+    """Rows [row0, row0 + nrows) of the sector CSR, built by the oracle (literal
+    operator products applied to each row state)."""
+    import scipy.sparse as sp
+    from oracle import sector as osec
+    rows = np.arange(row0, row0 + nrows, dtype=np.int64)
+    ptr, cols, vals = osec.row_entries(model, n_up, n_dn, rows)
+    dim = W_sector_dim(model.n_s, n_up, n_dn)
+    return sp.csr_matrix((vals, cols.astype(np.int32), ptr), shape=(nrows, dim))
+
+
+def W_sector_dim(n_s, n_up, n_dn):
+    import workloads as W
+    return W.sector_dim(n_s, n_up, n_dn)
+
+
+def time_loop(f, seconds, min_reps=3):
+    f()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        f()
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= seconds:
+            return el / reps, reps
+
+
+def cpu_baseline(model, x, prec, seconds, legs=True):
+    """The CPU oracle timed on this host: its sector H*v (SciPy CSR product over
+    the oracle-built matrix) on a contiguous block of rows of the same sector,
+    one core (the reported value); the same CSR through torch on every core; the
+    oracle's literal-operator product on random rows; and the oracle's
+    eigensolver wall-clock at the C0 and C1 sizes."""
     eb = 4 if prec == "fp32" else 8
-    return {"value": rate * 2 * eb / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} random rows of the (7,8) sector, oracle row-sampled H*v "
-                      f"(literal second-quantised operators, numpy, 1 thread), {el:.1f} s; "
-                      f"GB/s = rows/s x {2 * eb} B"}
+    cores = cpu_cores()
+    D_dn = W_sector_dim(NS, 0, NDN)
+    nrows = D_dn * 96                                       # 96 up strings, ~1.5% of the sector's rows
+    row0 = D_dn * (W_sector_dim(NS, NUP, 0) // 2)           # from the middle of the row order
+    t0 = time.perf_counter()
+    A = oracle_csr_block(model, NUP, NDN, row0, nrows)
+    t_build = time.perf_counter() - t0
+    x64 = np.asarray(x, dtype=np.float64)
+    per, reps = time_loop(lambda: A @ x64, seconds / 2)
+    rows_per_s = nrows / per
+    out = {"value": rows_per_s * 2 * eb / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"rows {row0}..{row0 + nrows - 1} ({nrows} rows, {A.nnz} stored entries) of the (7,8) "
+                     f"sector's CSR built by the oracle (literal operator products, {t_build:.1f} s), SciPy CSR "
+                     f"matvec on 1 core, {reps} products of {per * 1e3:.2f} ms; GB/s = rows/s x {2 * eb} B "
+                     f"(the metric's compulsory bytes per row)",
+           "cpu_model": cpu_model(), "host_cores": cores}
+    if not legs:
+        return out
+    out["legs"] = {}
+    try:
+        import torch
+        nt = torch.get_num_threads()
+        torch.set_num_threads(cores)
+        At = torch.sparse_csr_tensor(torch.from_numpy(A.indptr.astype(np.int64)),
+                                     torch.from_numpy(A.indices.astype(np.int64)),
+                                     torch.from_numpy(A.data), size=A.shape, check_invariants=False)
+        xt = torch.from_numpy(x64)
+        pt, rt = time_loop(lambda: At @ xt, seconds / 4)
+        torch.set_num_threads(nt)
+        out["legs"]["torch_sparse_csr_all_cores"] = {
+            "GB/s": nrows / pt * 2 * eb / 1e9, "threads": cores, "ms_per_product": pt * 1e3, "reps": rt,
+            "rows": nrows}
+    except Exception as e:  # torch without sparse CSR matmul on this host
+        out["legs"]["torch_sparse_csr_all_cores"] = {"unavailable": str(e)[:200]}
+    rng = np.random.default_rng(123)
+    rate, done, el = oracle_rows_rate(model, x64, seconds / 4, rng)
+    out["legs"]["literal_operator_rows_1_core"] = {"GB/s": rate * 2 * eb / 1e9, "rows": done, "seconds": el}
+    out["legs"]["oracle_eigensolver"] = oracle_eigsh_times()
+    return out
+
+
+def oracle_eigsh_times():
+    """Oracle lowest eigenvalue wall-clock (sector CSR built by the oracle, then
+    dense eigh up to dim 4900 or ARPACK eigsh): C0, the AIM N_s=6 (3,3) (dim
+    400), and C1, the Kanamori N_s=12 (6,6) (dim 853,776), ground state."""
+    import workloads as W
+    from oracle import sector as osec, spectrum
+    res = {}
+    for name, m, nu, nd in (("C0 AIM N_s=6 (3,3)", W.aim(6, seed=0), 3, 3),
+                            ("C1 Kanamori N_s=12 (6,6)", W.kanamori(12, seed=0), 6, 6)):
+        t0 = time.perf_counter()
+        H = osec.build_csr(m, nu, nd)
+        t1 = time.perf_counter()
+        w = spectrum.lowest(H, 1)
+        t2 = time.perf_counter()
+        res[name] = {"dim": int(H.shape[0]), "build_s": t1 - t0, "eigensolve_s": t2 - t1, "E0": float(w[0])}
+    return res
 
 
 def row_kernel(prec):
     """The fast row kernel that ed_apply_h launches, untuned, for this vector format."""
-    return "k_apply_pair" if prec == "fp32" else "k_apply_win"
+    return "k_apply_nat" if prec == "fp32" else "k_apply_win"
 
 
 def row_kernel_of(kernel_id):
     """Kernel name of an ed_sector_info / ed_tune_result kernel id."""
-    return {2: "k_apply_win", 3: "k_apply_pair"}.get(kernel_id, f"generic_{kernel_id}")
+    return {2: "k_apply_win", 3: "k_apply_pair", 4: "k_apply_nat"}.get(kernel_id, f"generic_{kernel_id}")
 
 
 def traffic_for(kernel_src_sha, prec, kernel=None):
@@ -219,7 +328,7 @@ def traffic_for(kernel_src_sha, prec, kernel=None):
 
 def src_sha():
     h = hashlib.sha256()
-    for f in ("apply_fast.cu", "ed_internal.h"):
+    for f in ("apply_fast.cu", "apply_nat.cu", "ed_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1004_3354_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -304,59 +413,36 @@ def run_ours(a):
     ms_step = total_ms / a.steps
     nbytes = alg_bytes(a.prec, dim)
 
-    # end to end: pinned host x -> device, H*v, device -> pinned host y, every
-    # step.  Steps are pipelined on three streams with two device buffers each
-    # way: the copy-in of step i+1 and the copy-out of step i-1 overlap the
-    # H*v of step i (the host link carries both directions at once).
+    # end to end through the C ABI with host buffers: ed_apply_h_host takes
+    # e2e_steps vectors in pinned host memory, copies each in, applies H and
+    # copies each result out, pipelined on its internal streams (the copy-in of
+    # step i+1 and the copy-out of step i-1 overlap H*v of step i)
     h2d = d2h = dim * (4 if a.prec == "fp32" else 8)
-    hx = [torch.empty(dim * epv, dtype=tdt, pin_memory=True) for _ in range(2)]
-    hy = [torch.empty(dim * epv, dtype=tdt, pin_memory=True) for _ in range(2)]
-    for h in hx:
-        h.copy_(x.cpu())
-    xd = [x, torch.empty_like(x)]
-    yd = [y, torch.empty_like(y)]
-    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-
-    def pipeline(n):
-        h2d_done = [torch.cuda.Event() for _ in range(2)]
-        app_done = [torch.cuda.Event() for _ in range(2)]
-        d2h_done = [torch.cuda.Event() for _ in range(2)]
-        for i in range(n):
-            b = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(app_done[b])        # step i-2 finished reading xd[b]
-                xd[b].copy_(hx[b], non_blocking=True)
-                h2d_done[b].record(s_in)
-            s_cmp.wait_event(h2d_done[b])
-            if i >= 2:
-                s_cmp.wait_event(d2h_done[b])           # step i-2's result has left yd[b]
-            ed.ed_apply_h(sec, xd[b], yd[b], s_cmp)
-            app_done[b].record(s_cmp)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(app_done[b])
-                hy[b].copy_(yd[b], non_blocking=True)
-                d2h_done[b].record(s_out)
-
-    pipeline(4)
+    n_e2e = max(2, a.e2e_steps)
+    xh1 = x.cpu()
+    hx = torch.empty(n_e2e * xh1.numel(), dtype=tdt).pin_memory()
+    for i in range(n_e2e):
+        hx[i * xh1.numel():(i + 1) * xh1.numel()].copy_(xh1)
+    hy = torch.empty_like(hx).pin_memory()
+    ed.ed_apply_h_host(sec, 2, hx, hy, stream)          # warm-up: makes the transfer buffers
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s_in)
-    s_cmp.wait_event(e0)
-    s_out.wait_event(e0)
-    pipeline(a.e2e_steps)
-    s_out.wait_stream(s_in)
-    s_out.wait_stream(s_cmp)
-    e1.record(s_out)
+    e0.record(stream)
+    ed.ed_apply_h_host(sec, n_e2e, hx, hy, stream)
+    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / a.e2e_steps
+    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    del hx, hy
     ms_step, e2e_ms = ranks_max([ms_step, e2e_ms], dist, "cuda")
     value = whole_job_gbs(world, nbytes, ms_step)
     e2e = {"value": whole_job_gbs(world, nbytes, e2e_ms), "unit": "GB/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": a.e2e_steps,
-           "what": "pinned host x -> device, ed_apply_h, device -> pinned host y, every step; steps pipelined "
-                   "on three streams (copy-in of step i+1 and copy-out of step i-1 overlap H*v of step i)"}
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": n_e2e,
+           "what": "one ed_apply_h_host C-ABI call on e2e_steps vectors in pinned host memory: every step's x "
+                   "copied host -> device and y device -> host inside the call, pipelined on the library's "
+                   "internal streams with the applies"}
 
     extras = {}
     if not a.no_extras and rank == 0:
@@ -387,6 +473,12 @@ def run_ours(a):
             del xq, yq
             ed.ed_sector_destroy(s2)
 
+    # the serving half of the metric (solves/s and p99 latency vs plain FP64),
+    # a bounded run of the request stream on rank 0 of a one-GPU job
+    serve = None
+    if not a.no_serve and rank == 0 and world == 1:
+        serve = serve_bench(ed, ctx, torch, n_req=a.serve_requests, k=4, tol=a.serve_tol, precs=("fp32",))
+
     info = ed.ed_sector_get_info(sec)
     peak, src = peaks()
     avg_launch = statistics.mean(launch_ms)
@@ -406,6 +498,7 @@ def run_ours(a):
         "alu_roofline": alu_roofline(a.prec, dim, info.nnz_per_row, statistics.mean(launch_ms)),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": a.steps,
         "clocks": clk, "nnz_per_row": round(info.nnz_per_row, 3), "other_formats": extras, "autotune": tuned,
+        "serve": serve,
     }
     ed.ed_sector_destroy(sec)
     ed.ed_ctx_destroy(ctx)
@@ -416,6 +509,9 @@ def run_ours(a):
 
 
 def run_reference(a):
+    """The reference arm: the CPU oracle's sector H*v (SciPy CSR product over the
+    oracle-built matrix, one core) on a block of rows of the same N_s=15 (7,8)
+    sector, one product per step; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -423,26 +519,29 @@ def run_reference(a):
     model = W.kanamori(NS, seed=SEED)
     dim = W.sector_dim(NS, NUP, NDN)
     x = W.random_vector(dim, seed=1)
-    rng = np.random.default_rng(7)
-    per_step = max(1.0, min(4.0, 120.0 / max(1, a.steps + a.warmup)))
-    for _ in range(a.warmup):
-        oracle_rows_rate(model, x, per_step, rng)
-    rates, t0 = [], time.perf_counter()
-    rows_total = 0
+    D_dn = W_sector_dim(NS, 0, NDN)
+    nrows = D_dn * 96
+    row0 = D_dn * (W_sector_dim(NS, NUP, 0) // 2)
+    t0 = time.perf_counter()
+    A = oracle_csr_block(model, NUP, NDN, row0, nrows)
+    t_build = time.perf_counter() - t0
+    for _ in range(max(1, a.warmup)):
+        A @ x
+    t0 = time.perf_counter()
     for _ in range(a.steps):
-        r, done, el = oracle_rows_rate(model, x, per_step, rng)
-        rates.append(r)
-        rows_total += done
+        A @ x
     el = time.perf_counter() - t0
     eb = 4 if a.prec == "fp32" else 8
-    value = rows_total / el * 2 * eb / 1e9
+    value = nrows * a.steps / el * 2 * eb / 1e9
+    sample = (f"{a.steps} products over rows {row0}..{row0 + nrows - 1} ({nrows} rows, {A.nnz} stored entries) of "
+              f"the (7,8) sector's CSR built by the oracle ({t_build:.1f} s, not timed), SciPy CSR matvec, 1 core; "
+              f"GB/s = rows/s x {2 * eb} B")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 0,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random bath)",
            "config": workload_config(a.prec, dim),
-           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{rows_total} random rows over {a.steps} steps of ~{per_step:.1f} s, "
-                                      f"oracle row-sampled H*v, numpy, 1 thread"},
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model(), "host_cores": cpu_cores()},
            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -502,82 +601,152 @@ def run_sectors12(a):
     print(json.dumps(out), flush=True)
 
 
-def run_serve(a):
+def tr_basis(k):
+    """Thick-restart basis the request server uses for a k > 1 request."""
+    return min(max(4 * k + 8, 20), 64)
+
+
+def serve_golden():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "serve_stream.json")) as f:
+            g = json.load(f)
+        return {r["id"]: r for r in g["requests"]}, g["greens"]["n"]
+    except (OSError, KeyError, ValueError):
+        return {}, []
+
+
+def oracle_errors(results, golden, pts, k):
+    """Max relative error of the k lowest energies and max |G - G_oracle| over
+    the requests the oracle solved (tests/golden/serve_stream.json)."""
+    e_err, g_err, n = 0.0, 0.0, 0
+    for q, res in results.items():
+        if q not in golden or res["E"] is None:
+            continue
+        ref = np.array(golden[q]["E"][:k])
+        E = np.array(res["E"][:len(ref)])
+        e_err = max(e_err, float(np.max(np.abs(E - ref) / np.abs(ref))))
+        if res["G"] is not None and pts:
+            Gr = np.array(golden[q]["G_re"]) + 1j * np.array(golden[q]["G_im"])
+            g_err = max(g_err, float(np.max(np.abs(res["G"][pts] - Gr))))
+        n += 1
+    return {"requests_checked": n, "max_rel_E_err_vs_oracle": e_err if n else None,
+            "max_abs_G_err_vs_oracle": g_err if n else None}
+
+
+def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=("saturation", "poisson"),
+                served_fp64=False, max_active=16):
     """Impurity-solve requests (three-orbital Kanamori, N_s uniform in 10..16,
-    ground sector around half filling, G(i w_n) of orbital 0 spin up on 1024
-    Matsubara points at beta = 40, CF depth 100) served with continuous
-    batching, against the plain FP64 path solving them one at a time."""
-    import torch
-    import paper_1004_3354_gb300 as ed
+    sector ((N+1)/2, N/2), k lowest states and G(i w_n) of orbital 0 spin up
+    from them, Boltzmann weights at beta = 40, 1024 Matsubara points, CF depth
+    100) through the request server, against the same library's plain FP64
+    path solving them one at a time (default kernels, the same thick-restart
+    solver and tolerance, no server, no concurrency).  The plain path's Poisson
+    latencies are those of a first-come-first-served queue over its measured
+    service times at the same arrival times."""
     import workloads as W
-    if not os.path.exists(ed.LIB_PATH):
-        from paper_1004_3354_gb300 import _build
-        _build.build()
-    torch.cuda.set_device(0)
-    beta, nw, depth, tol = 40.0, 1024, 100, 1e-10
-    stream = W.serving_stream(a.requests, seed=0, rate=1.0, ns_range=(10, 16))
+    beta, nw, depth = 40.0, 1024, 100
+    stream = W.serving_stream(n_req, seed=0, rate=1.0, ns_range=(10, 16))
     models = [W.kanamori(r["n_s"], seed=r["model_seed"]) for r in stream]
-    ctx = ed.ed_ctx_create(0)
-    # plain FP64, one at a time (no batching, no graphs, FP64 vectors)
-    base_E, base_lat = [], []
+    golden, pts = serve_golden()
+    m_b = tr_basis(k)
+    # plain FP64, one request at a time
+    service, base = [], {}
     t_all = time.perf_counter()
-    for r, m in zip(stream, models):
+    for q, (r, m) in enumerate(zip(stream, models)):
         t0 = time.perf_counter()
-        sec = ed.ed_sector_create(ctx, m, r["n_up"], r["n_dn"], "fp64", ed.ED_SECTOR_GENERIC)
+        sec = ed.ed_sector_create(ctx, m, r["n_up"], r["n_dn"], "fp64")
         dim = ed.ed_sector_get_info(sec).dim
-        psi = torch.empty(dim, dtype=torch.float64, device="cuda")
-        ev, info, st = ed.ed_lanczos(sec, k=1, tol=tol, max_iter=400, reorth=False, evecs=psi,
-                                     allow_not_converged=True)
-        ed.ed_greens_cf(ctx, m, "fp64", [(r["n_up"], r["n_dn"], float(ev[0]), psi)], beta, nw, orbital=m.orb0,
-                        spin=0, depth=depth)
+        kk = min(k, dim)
+        vecs = torch.empty(kk * dim, dtype=torch.float64, device="cuda")
+        ev, info, st = ed.ed_lanczos_tr(sec, k=kk, tol=tol, max_basis=min(m_b, dim), keep=0, max_iter=3000,
+                                        check_every=4, evecs=vecs, allow_not_converged=True)
+        states = [(r["n_up"], r["n_dn"], float(ev[j]), vecs[j * dim:(j + 1) * dim]) for j in range(kk)]
+        G = ed.ed_greens_cf(ctx, m, "fp64", states, beta, nw, orbital=m.orb0, spin=0, depth=depth)
+        torch.cuda.synchronize()
         ed.ed_sector_destroy(sec)
-        del psi
-        base_E.append(float(ev[0]))
-        base_lat.append(1e3 * (time.perf_counter() - t0))
+        del vecs, states
+        service.append(time.perf_counter() - t0)
+        base[q] = {"E": [float(e) for e in ev], "G": G, "status": st}
     base_total = time.perf_counter() - t_all
-    base_rate = len(stream) / base_total
-    out = {"metric": "impurity solves/s served (N_s 10..16, ground state + G(i w_n))", "unit": "solves/s",
-           "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded random baths, Poisson arrivals)",
-           "config": {"workload": f"{len(stream)} requests, three-orbital Kanamori N_s~U{{10..16}}, "
-                                  f"sector ((N+1)/2, N/2), tol {tol}, CF depth {depth}, n_w {nw}, beta {beta}"},
-           "plain_fp64_one_at_a_time": {"solves_per_s": base_rate, "seconds": base_total,
-                                        "p50_ms": float(np.percentile(base_lat, 50)),
-                                        "p99_ms": float(np.percentile(base_lat, 99))}}
+    base_rate = n_req / base_total
+    rate = 0.8 * base_rate                      # open-loop arrivals at 0.8x plain capacity
+    arrivals = [r["t_arrive"] / rate for r in stream]
+    fin, lat_sat, lat_poi = 0.0, [], []
+    for s_, a_ in zip(service, arrivals):       # FIFO queue over the measured service times
+        lat_sat.append(sum(service[:len(lat_sat) + 1]) * 1e3)
+        fin = max(fin, a_) + s_
+        lat_poi.append((fin - a_) * 1e3)
+    out = {"requests": n_req, "k": k, "tol": tol, "cf_depth": depth, "n_w": nw, "beta": beta,
+           "thick_restart_basis": m_b,
+           "workload": f"{n_req} requests, three-orbital Kanamori N_s~U{{10..16}}, sector ((N+1)/2, N/2), "
+                       f"k={k} lowest + G(i w_n) from them",
+           "plain_fp64_one_at_a_time": {
+               "solves_per_s": base_rate, "seconds": base_total,
+               "saturation": {"p50_ms": float(np.percentile(lat_sat, 50)), "p99_ms": float(np.percentile(lat_sat, 99))},
+               "poisson": {"p50_ms": float(np.percentile(lat_poi, 50)), "p99_ms": float(np.percentile(lat_poi, 99)),
+                           "arrival_rate_per_s": rate},
+               "not_converged": sum(1 for v in base.values() if v["status"] != 0),
+               **oracle_errors(base, golden, pts, k)}}
     budget = 200 * 1024 ** 3
-    for prec in ("fp32", "df64"):
-        for mode in ("saturation", "poisson"):
-            srv = ed.ed_server_create(ctx, hbm_budget=budget, max_active=16, prec=prec, tol=tol if prec != "fp32" else 1e-6,
-                                      max_iter=400, cf_depth=depth, n_w=nw, beta=beta)
-            rate = 0.8 * base_rate
-            arrivals = [0.0] * len(stream) if mode == "saturation" else [r["t_arrive"] / rate for r in stream]
-            tickets, results = [None] * len(stream), {}
+    for prec in list(precs) + (["fp64"] if served_fp64 else []):
+        for mode in modes:
+            srv = ed.ed_server_create(ctx, hbm_budget=budget, max_active=max_active, prec=prec, tol=tol,
+                                      max_iter=3000, cf_depth=depth, n_w=nw, beta=beta)
+            arr = [0.0] * n_req if mode == "saturation" else arrivals
+            tickets, results = [None] * n_req, {}
             t0 = time.perf_counter()
             i = 0
-            while len(results) < len(stream):
+            while len(results) < n_req:
                 now = time.perf_counter() - t0
-                while i < len(stream) and arrivals[i] <= now:
-                    tickets[i] = ed.ed_submit(srv, models[i], stream[i]["n_up"], stream[i]["n_dn"])
+                while i < n_req and arr[i] <= now:
+                    tickets[i] = ed.ed_submit(srv, models[i], stream[i]["n_up"], stream[i]["n_dn"], k=k)
                     i += 1
                 for q in range(i):
                     if q in results:
                         continue
                     done, res, G = ed.ed_poll(srv, tickets[q])
                     if done:
-                        results[q] = (res.status, res.E0, res.latency_ms)
+                        results[q] = {"status": res.status, "E": [res.E[j] for j in range(res.n_E)], "G": G,
+                                      "lat": res.latency_ms, "iters": res.iters,
+                                      "error": ed.last_error() if res.status != 0 else None}
                 time.sleep(0.0005)
             el = time.perf_counter() - t0
             stats = ed.ed_server_get_stats(srv)
             ed.ed_server_destroy(srv)
-            lat = [results[q][2] for q in range(len(stream))]
-            relerr = max(abs(results[q][1] - base_E[q]) / abs(base_E[q]) for q in range(len(stream)))
+            lat = [results[q]["lat"] for q in range(n_req)]
+            e_vs_plain = max(abs(results[q]["E"][0] - base[q]["E"][0]) / abs(base[q]["E"][0]) for q in range(n_req))
             out[f"served_{prec}_{mode}"] = {
-                "solves_per_s": len(stream) / el, "seconds": el, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "max_rel_E0_err_vs_fp64": relerr,
-                "failed": sum(1 for q in results if results[q][0] != 0), "max_active_seen": stats.max_active_seen,
-                "arrival_rate_per_s": None if mode == "saturation" else rate}
+                "solves_per_s": n_req / el, "seconds": el, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "failed": stats.failed,
+                "not_converged": sum(1 for q in results if results[q]["status"] == ed.ED_ERR_NOT_CONVERGED),
+                "errors": sorted({f"{stream[q]['n_s']}: {results[q]['status']} {results[q]['error']}"
+                                  for q in results if results[q]["status"] != 0})[:8],
+                "max_iters": max(results[q]["iters"] for q in results),
+                "max_active_seen": stats.max_active_seen, "arrival_rate_per_s": None if mode == "saturation" else rate,
+                "max_rel_E0_diff_vs_plain_fp64": e_vs_plain, **oracle_errors(results, golden, pts, k)}
+    if "served_fp32_saturation" in out:
+        out["speedup_served_fp32_vs_plain_fp64"] = out["served_fp32_saturation"]["solves_per_s"] / base_rate
+    return out
+
+
+def run_serve(a):
+    """The request stream of the serving configuration (N_s 10..16, k = 4 lowest
+    states + G per request) through the request server in every vector format,
+    saturation and Poisson arrivals, against the plain FP64 path one at a time."""
+    import torch
+    import paper_1004_3354_gb300 as ed
+    if not os.path.exists(ed.LIB_PATH):
+        from paper_1004_3354_gb300 import _build
+        _build.build()
+    torch.cuda.set_device(0)
+    ctx = ed.ed_ctx_create(0)
+    r = serve_bench(ed, ctx, torch, n_req=a.requests, k=4, tol=a.serve_tol, precs=("fp32", "df64"),
+                    served_fp64=True)
     ed.ed_ctx_destroy(ctx)
-    out["value"] = out["served_fp32_saturation"]["solves_per_s"]
-    out["speedup_served_fp32_vs_plain_fp64"] = out["value"] / base_rate
+    out = {"metric": "impurity solves/s served (N_s 10..16, 4 lowest states + G(i w_n))", "unit": "solves/s",
+           "higher_is_better": True, "n_gpus": 1, "data": "synthetic (seeded random baths, Poisson arrivals)",
+           "config": {"workload": r["workload"], "tol": a.serve_tol}, **r}
+    out["value"] = r["served_fp32_saturation"]["solves_per_s"]
     print(json.dumps(out), flush=True)
 
 
