@@ -55,3 +55,32 @@ def test_row_kernel_names():
     assert bench.row_kernel("fp32") == "k_apply_nat" and bench.row_kernel("df64") == "k_apply_win"
     assert bench.row_kernel_of(2) == "k_apply_win" and bench.row_kernel_of(3) == "k_apply_pair"
     assert bench.row_kernel_of(4) == "k_apply_nat"
+
+
+def test_serve_oracle_errors_match_requests_by_model():
+    """Served energies are compared with the oracle golden only for requests
+    whose model seed, N_s and sector match the golden entry (streams of other
+    lengths draw other N_s for the same request index)."""
+    stream = [{"n_s": 10, "model_seed": 1000, "n_up": 5, "n_dn": 5},
+              {"n_s": 11, "model_seed": 1001, "n_up": 6, "n_dn": 5}]
+    golden = {0: {"n_s": 10, "model_seed": 1000, "sector": [5, 5], "E": [-2.0, -1.0], "G_re": [0.5], "G_im": [-0.5]},
+              1: {"n_s": 12, "model_seed": 1001, "sector": [6, 6], "E": [-9.0, -8.0], "G_re": [0.0], "G_im": [0.0]}}
+    import numpy as np
+    res = {0: {"E": [-2.0 * (1 + 1e-9), -1.0], "G": np.array([0.5 - 0.5j + 1e-7])},
+           1: {"E": [-1.0, 0.0], "G": np.array([1.0 + 0j])}}
+    r = bench.oracle_errors(res, golden, [0], 2, stream)
+    assert r["requests_checked"] == 1                      # request 1 is another model
+    assert r["max_rel_E_err_vs_oracle"] == pytest.approx(1e-9, rel=1e-6)
+    assert r["max_abs_G_err_vs_oracle"] == pytest.approx(1e-7, rel=1e-6)
+    assert bench.oracle_errors(res, {}, [], 2, stream)["requests_checked"] == 0
+
+
+def test_serve_fifo_latencies():
+    """The plain path's latencies: a first-come-first-served queue over the
+    measured service times."""
+    # all at t = 0: each waits for the ones before it
+    assert bench.fifo_latencies_ms([1.0, 2.0, 0.5], [0.0, 0.0, 0.0]) == pytest.approx([1000, 3000, 3500])
+    # sparse arrivals: no queueing; a burst: the second waits
+    assert bench.fifo_latencies_ms([1.0, 1.0], [0.0, 5.0]) == pytest.approx([1000, 1000])
+    assert bench.fifo_latencies_ms([1.0, 1.0, 1.0], [0.0, 0.5, 10.0]) == pytest.approx([1000, 1500, 1000])
+    assert bench.tr_basis(4) == 24 and bench.tr_basis(1) == 20 and bench.tr_basis(16) == 64
