@@ -78,6 +78,8 @@ typedef enum ed_prec { ED_PREC_FP64 = 0, ED_PREC_DF64 = 1, ED_PREC_FP32 = 2 } ed
 /* Sector creation flags. */
 #define ED_SECTOR_CSR 1u      /* also build the stored CSR matrix (Fig. 1 layout), FP64 only */
 #define ED_SECTOR_GENERIC 2u  /* skip the row-kernel tables: H*v uses the generic kernels only */
+#define ED_SECTOR_ACC_DF 4u   /* FP32 vectors: keep double-float sums in H*v (the two-row kernel)
+                                 instead of the natural-order kernel's float sums */
 
 typedef struct ed_ctx ed_ctx;
 typedef struct ed_sector ed_sector;

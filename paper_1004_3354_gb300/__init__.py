@@ -24,6 +24,7 @@ ED_PREC_FP64, ED_PREC_DF64, ED_PREC_FP32 = 0, 1, 2
 ED_SPIN_UP, ED_SPIN_DN = 0, 1
 ED_SECTOR_CSR = 1
 ED_SECTOR_GENERIC = 2
+ED_SECTOR_ACC_DF = 4
 ED_MAX_K = 64
 PREC_NAMES = {"fp64": ED_PREC_FP64, "df64": ED_PREC_DF64, "fp32": ED_PREC_FP32}
 STATUS_NAMES = {0: "ED_OK", 1: "ED_ERR_INVALID", 2: "ED_ERR_OOM", 3: "ED_ERR_CUDA", 4: "ED_ERR_TIMEOUT",

@@ -249,9 +249,10 @@ int ed_sector_create(ed_ctx* ctx, const ed_model* model, int n_up, int n_dn, int
   ED_GUARD_BEGIN
   if (!ctx || !model || !out) ED_INVALID("NULL argument");
   *out = nullptr;
-  if (flags & ~(ED_SECTOR_CSR | ED_SECTOR_GENERIC)) ED_INVALID("unknown flags 0x%x", flags);
+  if (flags & ~(ED_SECTOR_CSR | ED_SECTOR_GENERIC | ED_SECTOR_ACC_DF)) ED_INVALID("unknown flags 0x%x", flags);
   ed_sector* h = new ed_sector();
   int st = build_sector(&ctx->c, model, n_up, n_dn, prec, &h->s);
+  h->s.acc_df = (flags & ED_SECTOR_ACC_DF) != 0;
   if (st == ED_OK && !(flags & ED_SECTOR_GENERIC)) st = build_fast(&h->s);
   if (st == ED_OK && (flags & ED_SECTOR_CSR)) st = build_csr(&h->s);
   if (st != ED_OK) {

@@ -1074,17 +1074,14 @@ bool fast_variant_applies(const Sector* s, int v) {
   return v < kNShapes || s->fast.pair_ok;
 }
 
-// Untuned choice: the natural-order kernel for float sectors that have it, four
-// rows per block while two such blocks fit an SM's shared memory, else two;
+// Untuned choice: the natural-order kernel for float sectors that have it (two
+// rows per block, 256 threads, three blocks per SM where they fit);
 // otherwise two rows per block for float vectors, one otherwise; 256
 // threads x 3 blocks per SM while three staged blocks fit the SM's shared
 // memory, else 384 x 2 (24 warps either way; measured at N_s = 16, where
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
-  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
-    const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
-    return kNatBase + (2 * (nat_variant_smem(s, 0) + 1024) <= per_sm ? 0 : 3);
-  }
+  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) return kNatBase + 3;  // two rows, 256 x 3 (0.349 ms at N_s = 15)
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;
   const uint32_t D = s->dn.D;
   const int nc = s->fast.n_coef;

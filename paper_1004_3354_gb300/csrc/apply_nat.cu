@@ -547,6 +547,7 @@ int build_nat(Sector* s, const std::vector<double>& coef, int zero_id) {
   auto& f = s->fast;
   f.nat_ok = false;
   if ((s->prec != ED_PREC_FP32 && s->prec != ED_PREC_DF64) || !f.ok) return ED_OK;
+  if (s->prec == ED_PREC_FP32 && s->acc_df) return ED_OK;  // the caller keeps double-float sums
   if (s->n_mix && !f.mix_delta) return ED_OK;
   if (f.n_pat > kMaxPatN || (int)coef.size() > kMaxCoefN) return ED_OK;
   if (f.mix_delta && s->M * s->M * (1 << s->M) > kMaxDeltaN) return ED_OK;

@@ -224,6 +224,8 @@ struct Sector {
   } fast;
   // autotuned H*v variant of the fast path (apply_fast.cu), -1 = untuned
   int tune = -1;
+  // FP32 vectors with double-float sums (ED_SECTOR_ACC_DF): no natural-order tables
+  bool acc_df = false;
   // stored CSR (optional)
   uint64_t csr_nnz = 0;
   uint64_t* csr_ptr = nullptr;

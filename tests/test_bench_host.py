@@ -41,7 +41,7 @@ def test_alu_ceiling_arithmetic():
     assert bench.alu_roofline("fp32", dim, nnz, 0.5)["ops_per_launch"] == pytest.approx(dim * (nnz + 1.0))
 
 
-@pytest.mark.parametrize("prec,kernel", [("df64", "k_apply_win"), ("fp32", "k_apply_pair"), ("fp64", "k_apply_win")])
+@pytest.mark.parametrize("prec,kernel", [("df64", "k_apply_win"), ("fp32", "k_apply_nat"), ("fp64", "k_apply_win")])
 def test_traffic_only_for_the_captured_source(prec, kernel):
     p = os.path.join(ROOT, "profiles", f"{kernel}_{prec}_n15_traffic.txt")
     kv = dict(line.split(":", 1) for line in open(p) if ":" in line)

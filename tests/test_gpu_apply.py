@@ -276,3 +276,21 @@ def test_apply_host_buffers_pipeline(env, prec):
             ed.ed_apply_h_host(sec, 1, None, hy1)
     finally:
         ed.ed_sector_destroy(sec)
+
+
+def test_fp32_vectors_with_double_float_sums(env):
+    """ED_SECTOR_ACC_DF: float vectors whose H*v keeps double-float sums (the
+    two-row kernel) round each element once, so every element is within 2^-24
+    relative of the oracle applied to the float input; the default
+    (natural-order kernel, float sums) stays within its stated bound."""
+    ed, ctx, torch = env
+    m = W.kanamori(12, seed=0)
+    H = oracle_csr("C1 Kanamori N_s=12 (6,6) full", m, 6, 6)
+    x = W.random_vector(H.shape[0], seed=1)
+    ref = H @ input_for("fp32", x)
+    y_df = run_apply(ed, ctx, torch, m, 6, 6, "fp32", x, ed.ED_SECTOR_ACC_DF, expect_kernel=3)
+    # one rounding to float, plus the double-float sum's own error (~2^-46 of sum |H_ij x_j|)
+    scale = abs(H) @ np.abs(input_for("fp32", x))
+    assert np.all(np.abs(y_df - ref) <= 2.0 ** -24 * np.abs(ref) + 2.0 ** -40 * scale)
+    y_nat = run_apply(ed, ctx, torch, m, 6, 6, "fp32", x, expect_kernel=4)
+    assert rel_err(y_nat, ref) <= 1e-6
