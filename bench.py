@@ -663,8 +663,49 @@ def oracle_errors(results, golden, pts, k, stream):
             "max_abs_G_err_vs_oracle": g_err if n else None}
 
 
+PACK_DIM = 250_000   # served requests with at most this many states are solved in packs (N_s <= 11 here)
+
+
+def serve_saturation(ed, ctx, stream, models, k, tol, prec, pack_dim, max_active=16, depth=100, nw=1024, beta=40.0):
+    """All requests submitted at t = 0; returns (seconds, failures, max active)."""
+    srv = ed.ed_server_create(ctx, hbm_budget=200 * 1024 ** 3, max_active=max_active, prec=prec, tol=tol,
+                              max_iter=3000, cf_depth=depth, n_w=nw, beta=beta, pack_dim=pack_dim)
+    t0 = time.perf_counter()
+    tickets = [ed.ed_submit(srv, m, r["n_up"], r["n_dn"], k=k) for r, m in zip(stream, models)]
+    done, fails = set(), 0
+    while len(done) < len(tickets):
+        for t in tickets:
+            if t in done:
+                continue
+            d, res, G = ed.ed_poll(srv, t)
+            if d:
+                done.add(t)
+                fails += int(res.status != 0)
+        time.sleep(0.0005)
+    el = time.perf_counter() - t0
+    mx = ed.ed_server_get_stats(srv).max_active_seen
+    ed.ed_server_destroy(srv)
+    return el, fails, mx
+
+
+def small_requests_bench(ed, ctx, n_req=32, k=4, tol=1e-8, prec="fp32"):
+    """Small impurity solves (N_s 8..11, the same request shape as the serving
+    stream) served one request per stream against packs of them (one batched
+    Lanczos over all their sectors per step)."""
+    import workloads as W
+    stream = W.serving_stream(n_req, seed=1, rate=1.0, ns_range=(8, 11))
+    models = [W.kanamori(r["n_s"], seed=r["model_seed"]) for r in stream]
+    out = {"requests": n_req, "k": k, "tol": tol, "prec": prec, "n_s": "8..11", "pack_dim": PACK_DIM}
+    for label, pd in (("one_stream_per_request", 0), ("packs", PACK_DIM)):
+        serve_saturation(ed, ctx, stream[:4], models[:4], k, tol, prec, pd)      # warm-up
+        el, fails, mx = serve_saturation(ed, ctx, stream, models, k, tol, prec, pd)
+        out[label] = {"solves_per_s": n_req / el, "seconds": el, "failed": fails, "max_active_seen": mx}
+    out["speedup_packs"] = out["packs"]["solves_per_s"] / out["one_stream_per_request"]["solves_per_s"]
+    return out
+
+
 def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=("saturation", "poisson"),
-                served_fp64=False, max_active=16):
+                served_fp64=False, max_active=16, pack_dim=PACK_DIM):
     """Impurity-solve requests (three-orbital Kanamori, N_s uniform in 10..16,
     sector ((N+1)/2, N/2), k lowest states and G(i w_n) of orbital 0 spin up
     from them, Boltzmann weights at beta = 40, 1024 Matsubara points, CF depth
@@ -704,7 +745,7 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
     lat_sat = fifo_latencies_ms(service, [0.0] * n_req)
     lat_poi = fifo_latencies_ms(service, arrivals)
     out = {"requests": n_req, "k": k, "tol": tol, "cf_depth": depth, "n_w": nw, "beta": beta,
-           "thick_restart_basis": m_b,
+           "thick_restart_basis": m_b, "pack_dim": pack_dim,
            "workload": f"{n_req} requests, three-orbital Kanamori N_s~U{{10..16}}, sector ((N+1)/2, N/2), "
                        f"k={k} lowest + G(i w_n) from them",
            "plain_fp64_one_at_a_time": {
@@ -718,7 +759,7 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
     for prec in list(precs) + (["fp64"] if served_fp64 else []):
         for mode in modes:
             srv = ed.ed_server_create(ctx, hbm_budget=budget, max_active=max_active, prec=prec, tol=tol,
-                                      max_iter=3000, cf_depth=depth, n_w=nw, beta=beta)
+                                      max_iter=3000, cf_depth=depth, n_w=nw, beta=beta, pack_dim=pack_dim)
             arr = [0.0] * n_req if mode == "saturation" else arrivals
             tickets, results = [None] * n_req, {}
             t0 = time.perf_counter()
@@ -753,6 +794,7 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
                 "max_rel_E0_diff_vs_plain_fp64": e_vs_plain, **oracle_errors(results, golden, pts, k, stream)}
     if "served_fp32_saturation" in out:
         out["speedup_served_fp32_vs_plain_fp64"] = out["served_fp32_saturation"]["solves_per_s"] / base_rate
+    out["small_requests"] = small_requests_bench(ed, ctx, k=k, tol=tol, prec=precs[0])
     return out
 
 

@@ -458,9 +458,19 @@ int ed_batch_autotune(ed_batch* b, int steps, ed_batch_tune_result* out, void* s
  *         server, then (want_G) G from those states with Boltzmann weights at
  *         beta (states below a weight of 1e-5 relative to the lowest skipped),
  *         as ed_greens_cf.
- * A request's kernels touch only its own buffers, so its result is bitwise the
- * same alone or in a mix.  The server's context must not be used from other
- * threads while the server runs. */
+ *  packs: requests whose sector has at most pack_dim states (small sectors,
+ *         whose single solves are bound by launch latency) are not run one by
+ *         one: the server takes every queued such request with the same k
+ *         (up to 64) and solves their sectors together, each Lanczos step one
+ *         replay of a CUDA graph whose kernels are single launches over all
+ *         their sectors (full CGS2 reorthogonalisation, at most 400 steps,
+ *         Ritz vectors from the stored basis), then forms each request's G
+ *         from its k states as above.  Packed requests do not take slots of
+ *         max_active; one pack runs at a time, on a worker thread.
+ * A request's kernels touch only its own buffers (and, in a pack, its own
+ * work items), so its result is bitwise the same alone or in a mix.  The
+ * server's context must not be used from other threads while the server
+ * runs. */
 #define ED_SERVE_MAX_K 16
 typedef struct ed_server ed_server;
 
@@ -474,6 +484,8 @@ typedef struct ed_server_opts {
   int n_w;             /* Matsubara frequencies */
   double beta;         /* inverse temperature */
   uint64_t seed;       /* start-vector seed */
+  uint64_t pack_dim;   /* requests whose sector has at most this many states are solved in packs
+                          (0: never); see below */
 } ed_server_opts;
 
 typedef struct ed_request {

@@ -93,7 +93,7 @@ class ed_batch_info(C.Structure):
 class ed_server_opts(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_active", C.c_int), ("prec", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("cf_depth", C.c_int), ("n_w", C.c_int), ("beta", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("pack_dim", C.c_uint64)]
 
 
 ED_SERVE_MAX_K = 16
@@ -508,9 +508,9 @@ def ed_batch_lanczos(b, n_sectors, k=8, tol=1e-10, max_iter=300, check_every=10,
 
 # ---------------------------------------------------------------- serving
 def ed_server_create(ctx, hbm_budget=0, max_active=8, prec=ED_PREC_FP64, tol=1e-10, max_iter=400, cf_depth=100,
-                     n_w=1024, beta=40.0, seed=1):
+                     n_w=1024, beta=40.0, seed=1, pack_dim=0):
     o = ed_server_opts(int(hbm_budget), int(max_active), PREC_NAMES.get(prec, prec), float(tol), int(max_iter),
-                       int(cf_depth), int(n_w), float(beta), int(seed))
+                       int(cf_depth), int(n_w), float(beta), int(seed), int(pack_dim))
     h = C.c_void_p()
     check(lib().ed_server_create(ctx, C.byref(o), C.byref(h)))
     h._n_w = int(n_w)

@@ -37,6 +37,7 @@ struct JobDev {
   uint64_t off;   // element offset inside every vector slot
   uint64_t dim;
   uint32_t item0, item1;
+  uint64_t seed_mix;  // start-vector hash term of the job (the same for a job alone or among others)
 };
 
 struct BatchDev {
@@ -382,9 +383,40 @@ __global__ void k_b_random(BatchDev B, V* __restrict__ w, uint64_t seed) {
     const JobDev& J = B.jobs[item.x];
     const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
     for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT) {
-      const uint64_t r = bmix(seed * 0x2545f4914f6cdd1dull + (uint64_t)item.x * 0x9e3779b97f4a7c15ull + e);
+      const uint64_t r = bmix(seed * 0x2545f4914f6cdd1dull + J.seed_mix + e);
       bset(w[J.off + e], (float)((r >> 40) * (1.0 / 16777216.0)) * 2.f - 1.f);
     }
+  }
+}
+
+// Ritz vectors of every job: out_q[i * dim + e] = sum_{j < m_q} S[q][i][j] V_j[e]
+// for i < min(k_q, m_q); jobs whose output pointer is NULL are skipped.
+__device__ __forceinline__ void rmac(double& a, double s, float2, double v) { a = fma(s, v, a); }
+__device__ __forceinline__ void rmac(float2& a, double, float2 s, float2 v) { df_mac(a, s, v); }
+__device__ __forceinline__ void rmac(float2& a, double, float2 s, float v) { df_mac1(a, s, v); }
+__device__ __forceinline__ double rout(double a, double*) { return a; }
+__device__ __forceinline__ float2 rout(float2 a, float2*) { return df_norm(a); }
+__device__ __forceinline__ float rout(float2 a, float*) { return __fadd_rn(a.x, a.y); }
+
+template <class V>
+__global__ void k_b_ritz(BatchDev B, const V* __restrict__ Vb, const double* __restrict__ S,
+                         const float2* __restrict__ Sf, const int* __restrict__ mj, const int* __restrict__ kj,
+                         int kmax, V* const* __restrict__ outs) {
+  using A = typename BAcc<V>::T;
+  for (uint32_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
+    const uint2 item = B.items[it];
+    V* out = outs[item.x];
+    if (!out) continue;
+    const JobDev& J = B.jobs[item.x];
+    const int m = mj[item.x], kq = min(kj[item.x], m);
+    const uint64_t e1 = min((uint64_t)item.y + B.chunk, J.dim);
+    for (uint64_t e = item.y + threadIdx.x; e < e1; e += kBT)
+      for (int i = 0; i < kq; ++i) {
+        const size_t row = ((size_t)item.x * kmax + i) * B.ms;
+        A acc{};
+        for (int j = 0; j < m; ++j) rmac(acc, S[row + j], Sf[row + j], Vb[(uint64_t)j * B.tot + J.off + e]);
+        out[(uint64_t)i * J.dim + e] = rout(acc, out);
+      }
   }
 }
 
@@ -488,9 +520,12 @@ struct RunBufs {
   }
 };
 
+// With ritz != NULL (one device pointer per job, NULL to skip a job) the k
+// lowest Ritz vectors of each job are written there, k consecutive vectors of
+// the job's dimension in the batch's format.
 template <class P>
 int batch_run(Batch* bt, const ed_lanczos_opts* o, double* evals, int* iters, ed_batch_info* info,
-              cudaStream_t user) {
+              cudaStream_t user, void* const* ritz = nullptr, int* conv = nullptr) {
   using V = typename P::V;
   auto t0 = std::chrono::steady_clock::now();
   Ctx* ctx = bt->ctx;
@@ -651,6 +686,15 @@ int batch_run(Batch* bt, const ed_lanczos_opts* o, double* evals, int* iters, ed
       if (iters) iters[q] = h_m[q];
       for (int i = 0; i < k; ++i) evals[(size_t)q * k + i] = (i < kc) ? h_theta[(size_t)q * kmax + i] : NAN;
     }
+  if (conv)
+    for (int q = 0; q < J; ++q) conv[q] = done[q];
+  if (ritz) {
+    V** douts = nullptr;
+    ED_TRY(R.alloc(&douts, J));
+    ED_TRY_CUDA(cudaMemcpyAsync(douts, ritz, sizeof(void*) * J, cudaMemcpyHostToDevice, st));
+    k_b_ritz<V><<<grid, kBT, 0, st>>>(B, Vb, S, Sf, dm, dk, kmax, douts);
+    ED_LAUNCH_CHECK();
+  }
   ED_TRY_CUDA(cudaStreamSynchronize(st));
   if (info) {
     info->steps = steps;
@@ -700,6 +744,7 @@ extern "C" int ed_batch_create(ed_ctx* ctx, const ed_model* model, int n_sectors
     jd.db = s->dn.basis;
     jd.off = off;
     jd.dim = s->dim;
+    jd.seed_mix = (uint64_t)q * 0x9e3779b97f4a7c15ull;
     b.hjobs.push_back(jd);
     off += (s->dim + 31) & ~(uint64_t)31;
     b.sectors.push_back(std::move(s));
@@ -731,15 +776,61 @@ extern "C" int ed_batch_destroy(ed_batch* h) {
 namespace ed {
 namespace {
 int batch_dispatch(Batch* b, const ed_lanczos_opts* opts, double* evals, int* iters, ed_batch_info* info,
-                   cudaStream_t user) {
+                   cudaStream_t user, void* const* ritz = nullptr, int* conv = nullptr) {
   switch (b->prec) {
-    case ED_PREC_FP64: return batch_run<PolF64>(b, opts, evals, iters, info, user);
-    case ED_PREC_DF64: return batch_run<PolDF>(b, opts, evals, iters, info, user);
-    default: return batch_run<PolF32>(b, opts, evals, iters, info, user);
+    case ED_PREC_FP64: return batch_run<PolF64>(b, opts, evals, iters, info, user, ritz, conv);
+    case ED_PREC_DF64: return batch_run<PolDF>(b, opts, evals, iters, info, user, ritz, conv);
+    default: return batch_run<PolF32>(b, opts, evals, iters, info, user, ritz, conv);
   }
 }
 bool chunk_ok(int c) { return c >= 64 && c <= 65536 && (c & (c - 1)) == 0; }
 }  // namespace
+
+// Sectors of different models solved together (the request server's packs of
+// small requests): n jobs, job q the sector (n_up[q], n_dn[q]) of *models[q],
+// all advanced by the same graph-replayed steps over one work list of `chunk`
+// elements per item.  A job's arithmetic depends only on its own sector, the
+// chunk and the seed, not on the other jobs, so its result is the same alone
+// or in any pack.  evals: n * k (NaN past a job's dimension); iters, conv
+// (1 where the job met tol or exhausted its Krylov space): n each; ritz: one
+// device pointer per job for its k Ritz vectors (or NULL).  The batch's tables
+// and vectors are made in ctx and released before returning.
+int batch_solve_pack(Ctx* ctx, int prec, int n, const ed_model* const* models, const int* n_up, const int* n_dn,
+                     const ed_lanczos_opts* o, uint32_t chunk, double* evals, int* iters, int* conv,
+                     void* const* ritz) {
+  Batch b;
+  b.ctx = ctx;
+  b.prec = prec;
+  b.n_jobs = n;
+  struct Rel {
+    Batch* b;
+    ~Rel() { b->release(); }
+  } rel{&b};
+  uint64_t off = 0;
+  for (int q = 0; q < n; ++q) {
+    std::unique_ptr<Sector> s(new Sector());
+    int st = build_sector(ctx, models[q], n_up[q], n_dn[q], prec, s.get());
+    if (st != ED_OK) {
+      free_sector(s.get());
+      return st;
+    }
+    JobDev jd{};
+    jd.S = s->view();
+    jd.ub = s->up.basis;
+    jd.db = s->dn.basis;
+    jd.off = off;
+    jd.dim = s->dim;
+    jd.seed_mix = 0;  // every job starts as it would alone
+    b.hjobs.push_back(jd);
+    off += (s->dim + 31) & ~(uint64_t)31;
+    b.sectors.push_back(std::move(s));
+  }
+  b.tot = off;
+  ED_TRY(b.alloc(&b.djobs, b.hjobs.size()));
+  ED_TRY(b.set_chunk(chunk));
+  ED_TRY_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+  return batch_dispatch(&b, o, evals, iters, nullptr, b.stream, ritz, conv);
+}
 }  // namespace ed
 
 extern "C" int ed_batch_set_chunk(ed_batch* h, int chunk) {

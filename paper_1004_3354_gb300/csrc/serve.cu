@@ -36,6 +36,9 @@ int trlan_run(Sector* s, const ed_trlan_opts* o, double* evals, void* evecs, ed_
 int greens_cf_run(Ctx* ctx, const ed_model* m, int prec, int n_states, const ed_state* states, double beta,
                   int n_w, const double* z, int orbital, int spin, int depth, double boltz_cut, double* G,
                   double* coeffs, cudaStream_t st);
+int batch_solve_pack(Ctx* ctx, int prec, int n, const ed_model* const* models, const int* n_up, const int* n_dn,
+                     const ed_lanczos_opts* o, uint32_t chunk, double* evals, int* iters, int* conv,
+                     void* const* ritz);
 int greens_accumulate(double2* dG, int n_w, double beta, const double* da, const double* db, int L, double n2,
                       const double* dE, int n_states, int nu, int sgn, cudaStream_t st);
 
@@ -157,8 +160,14 @@ struct Run3 {
   }
 };
 
-enum Phase { PH_QUEUED = 0, PH_GS, PH_GS_CHECK, PH_VEC, PH_CF, PH_CF_WAIT, PH_EVAL_WAIT, PH_WORK, PH_DONE,
+enum Phase { PH_QUEUED = 0, PH_GS, PH_GS_CHECK, PH_VEC, PH_CF, PH_CF_WAIT, PH_EVAL_WAIT, PH_WORK, PH_PACK, PH_DONE,
              PH_FAILED };
+
+// Packs of small requests: at most kMaxPack requests, Lanczos steps capped at
+// kPackIter (the basis holds them all), work items of kPackChunk elements.
+constexpr int kMaxPack = 64;
+constexpr int kPackIter = 400;
+constexpr uint32_t kPackChunk = 4096;
 
 // Thick-restart basis of a k > 1 request: max(4k + 8, 20) vectors, at most 64.
 inline int tr_basis(int k) { return std::min(std::max(4 * k + 8, 20), 64); }
@@ -169,6 +178,8 @@ struct Req {
   std::vector<double> T, U;
   ed_model model{};
   int n_up = 0, n_dn = 0, want_G = 1, orbital = 0, spin = 0, k = 1;
+  bool packed = false;      // solved in a pack of small requests
+  uint64_t dim = 0;
   Phase phase = PH_QUEUED;
   size_t footprint = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -252,6 +263,11 @@ struct Server : ServerBase {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::unique_ptr<Req<V>>> queue;
+  std::deque<std::unique_ptr<Req<V>>> pack_q;  // queued small requests
+  std::thread pack_th;                          // the running pack's worker
+  std::atomic<bool> pack_done{false};
+  bool pack_running = false;
+  std::vector<Req<V>*> pack_reqs;
   std::vector<std::unique_ptr<Req<V>>> active;
   std::map<uint64_t, std::unique_ptr<Req<V>>> finished;
   std::set<uint64_t> live;  // submitted and not yet collected
@@ -266,6 +282,7 @@ struct Server : ServerBase {
     stop = true;
     cv.notify_all();
     if (th.joinable()) th.join();
+    if (pack_th.joinable()) pack_th.join();
     // workers of k > 1 requests run to the end of their solve (release joins them)
     cudaSetDevice(ctx->device);
     for (auto& r : active) r->release();
@@ -283,6 +300,11 @@ struct Server : ServerBase {
     const double dcf = std::max({C(n_s, nu + 1) * C(n_s, nd), C(n_s, nu - 1) * C(n_s, nd),
                                  C(n_s, nu) * C(n_s, nd + 1), C(n_s, nu) * C(n_s, nd - 1)});
     const double eb = (double)elem_bytes(o.prec);
+    if (o.pack_dim && dim <= (double)o.pack_dim) {
+      // packed: the full Krylov basis and the k Ritz vectors, then the Green's function
+      const double steps = std::min<double>((double)std::min(o.max_iter, kPackIter), dim);
+      return (size_t)(((steps + 3.0 + k) * (dim + 32.0) + 6.0 * dcf) * eb + 64.0 * 1024 * 1024);
+    }
     if (k > 1) {
       // thick-restart basis (m + 2 + keep slots, padded) and the k Ritz vectors,
       // then the Green's function: both neighbour sectors' tables, phi and the
@@ -313,6 +335,16 @@ struct Server : ServerBase {
     if (q->k > ED_SERVE_MAX_K) ED_INVALID("k = %d outside 1..%d", r->k, ED_SERVE_MAX_K);
     q->ctx = ctx;
     q->footprint = estimate(m->n_s, r->n_up, r->n_dn, q->k);
+    {
+      auto C = [](int n, int k) -> uint64_t {
+        if (k < 0 || k > n) return 0;
+        uint64_t r = 1;
+        for (int i = 0; i < k; ++i) r = r * (uint64_t)(n - i) / (uint64_t)(i + 1);
+        return r;
+      };
+      q->dim = C(m->n_s, r->n_up) * C(m->n_s, r->n_dn);
+      q->packed = o.pack_dim && q->dim <= o.pack_dim;
+    }
     if (o.hbm_budget && q->footprint > o.hbm_budget) {
       set_error("request needs ~%zu bytes, more than the whole server budget %zu", q->footprint, o.hbm_budget);
       return ED_ERR_OOM;
@@ -424,6 +456,97 @@ struct Server : ServerBase {
       q->err = st == ED_ERR_NOT_CONVERGED ? "thick-restart Lanczos did not converge within max_iter" : buf;
     }
     q->wdone = true;
+  }
+
+  // ---- a pack of small requests with the same k: their sectors' Lanczos runs
+  // as one batched solve, then each request's Green's function; results are
+  // written into the requests, phases are set by the server thread
+  void run_pack(std::vector<Req<V>*> reqs) {
+    int st = solve_pack(reqs);
+    if (st != ED_OK) {
+      char buf[512];
+      ed_last_error(buf, sizeof(buf));
+      for (Req<V>* q : reqs)
+        if (q->status == ED_OK || q->status == ED_ERR_NOT_CONVERGED) {
+          q->status = st;
+          q->err = buf;
+        }
+    }
+    pack_done = true;
+  }
+
+  int solve_pack(std::vector<Req<V>*>& reqs) {
+    ED_TRY_CUDA(cudaSetDevice(ctx->device));
+    Ctx sub;
+    ED_TRY(make_sub_ctx(ctx, &sub));
+    struct SubGuard {
+      Ctx* c;
+      ~SubGuard() { free_sub_ctx(c); }
+    } sg{&sub};
+    cudaStream_t st = nullptr;
+    ED_TRY_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard {
+      cudaStream_t s;
+      ~StreamGuard() { cudaStreamDestroy(s); }
+    } stg{st};
+    const int n = (int)reqs.size(), k = reqs[0]->k;
+    std::vector<const ed_model*> models(n);
+    std::vector<int> nu(n), nd(n), it(n), conv(n);
+    std::vector<void*> ritz(n, nullptr);
+    std::vector<double> ev((size_t)n * k);
+    struct Free {
+      Ctx* c;
+      std::vector<std::pair<void*, size_t>> v;
+      ~Free() {
+        for (auto& a : v) dev_free(c, a.first, a.second);
+      }
+    } fr{&sub, {}};
+    for (int i = 0; i < n; ++i) {
+      models[i] = &reqs[i]->model;
+      nu[i] = reqs[i]->n_up;
+      nd[i] = reqs[i]->n_dn;
+      const size_t bytes = (size_t)std::min<uint64_t>((uint64_t)k, reqs[i]->dim) * reqs[i]->dim * sizeof(V);
+      ED_TRY(dev_alloc(&sub, &ritz[i], bytes));
+      fr.v.push_back({ritz[i], bytes});
+    }
+    ed_lanczos_opts lo{};
+    lo.k = k;
+    lo.tol = o.tol;
+    lo.max_iter = std::min(o.max_iter, kPackIter);
+    lo.check_every = 10;
+    lo.seed = o.seed;
+    lo.v0 = nullptr;
+    lo.reorth = 1;
+    const int bs = batch_solve_pack(&sub, o.prec, n, models.data(), nu.data(), nd.data(), &lo, kPackChunk,
+                                    ev.data(), it.data(), conv.data(), ritz.data());
+    if (bs != ED_OK && bs != ED_ERR_NOT_CONVERGED) return bs;
+    for (int i = 0; i < n; ++i) {
+      Req<V>* q = reqs[i];
+      const int kk = (int)std::min<uint64_t>((uint64_t)k, q->dim);
+      q->Ek.assign(ev.begin() + (size_t)i * k, ev.begin() + (size_t)i * k + kk);
+      q->E0 = ev[(size_t)i * k];
+      q->gs_iters = it[i];
+      if (!conv[i]) {
+        q->status = ED_ERR_NOT_CONVERGED;
+        q->err = "packed Lanczos did not converge within its step limit";
+      }
+      if (q->want_G) {
+        std::vector<ed_state> states(kk);
+        for (int j = 0; j < kk; ++j)
+          states[j] = ed_state{q->n_up, q->n_dn, q->Ek[j], static_cast<V*>(ritz[i]) + (size_t)j * q->dim};
+        q->G.assign(2 * (size_t)o.n_w, 0.0);
+        const int gs = greens_cf_run(&sub, &q->model, o.prec, kk, states.data(), o.beta, o.n_w, nullptr, q->orbital,
+                                     q->spin, o.cf_depth, 1e-5, q->G.data(), nullptr, st);
+        if (gs != ED_OK) {
+          char buf[512];
+          ed_last_error(buf, sizeof(buf));
+          q->status = gs;
+          q->err = buf;
+        }
+      }
+    }
+    ED_TRY_CUDA(cudaStreamSynchronize(st));
+    return ED_OK;
   }
 
   int check_work(Req<V>* q) {
@@ -662,14 +785,60 @@ struct Server : ServerBase {
   void loop() {
     cudaSetDevice(ctx->device);
     while (!stop) {
+      // a finished pack: its requests are done (or failed)
+      if (pack_running && pack_done) {
+        pack_th.join();
+        pack_running = false;
+        for (Req<V>* q : pack_reqs)
+          q->phase = (q->status == ED_OK || q->status == ED_ERR_NOT_CONVERGED) ? PH_DONE : PH_FAILED;
+        pack_reqs.clear();
+      }
+      // a new pack: the queued small requests with the first one's k, while their footprint fits
+      if (!pack_running) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pack_q.empty()) {
+          const int k = pack_q.front()->k;
+          std::deque<std::unique_ptr<Req<V>>> rest;
+          const double t_now = now_ms();
+          while (!pack_q.empty()) {
+            std::unique_ptr<Req<V>> q = std::move(pack_q.front());
+            pack_q.pop_front();
+            const bool fits = !o.hbm_budget || in_flight_bytes + q->footprint <= o.hbm_budget ||
+                              (active.empty() && pack_reqs.empty());
+            if (q->k != k || (int)pack_reqs.size() >= kMaxPack || !fits) {
+              rest.push_back(std::move(q));
+              continue;
+            }
+            in_flight_bytes += q->footprint;
+            q->t_admit = t_now;
+            q->phase = PH_PACK;
+            pack_reqs.push_back(q.get());
+            active.push_back(std::move(q));
+          }
+          pack_q = std::move(rest);
+          if (!pack_reqs.empty()) {
+            max_active_seen = std::max(max_active_seen, (int)active.size());
+            pack_done = false;
+            pack_running = true;
+            pack_th = std::thread([this, reqs = pack_reqs] { run_pack(reqs); });
+          }
+        }
+      }
       // admissions, first come first served, by HBM footprint and slot count
       for (;;) {
         std::unique_ptr<Req<V>> q;
         {
           std::lock_guard<std::mutex> lk(mu);
           if (queue.empty()) break;
+          if (queue.front()->packed) {  // small requests wait for the next pack
+            pack_q.push_back(std::move(queue.front()));
+            queue.pop_front();
+            continue;
+          }
           const size_t need = queue.front()->footprint;
-          if ((int)active.size() >= o.max_active) break;
+          int slots = 0;  // packed requests take no slot
+          for (auto& a : active) slots += a->packed ? 0 : 1;
+          if (slots >= o.max_active) break;
           if (o.hbm_budget && in_flight_bytes + need > o.hbm_budget && !active.empty()) break;
           q = std::move(queue.front());
           queue.pop_front();
@@ -682,9 +851,11 @@ struct Server : ServerBase {
         active.push_back(std::move(q));
         max_active_seen = std::max(max_active_seen, (int)active.size());
       }
-      bool idle = active.empty();
+      // nothing to drive on this thread when every active request waits on a worker
+      bool idle = true;
       for (auto& q : active) {
         if (q->phase == PH_DONE || q->phase == PH_FAILED) continue;
+        if (q->phase != PH_WORK && q->phase != PH_PACK) idle = false;
         int st = advance(q.get());
         if (st != ED_OK) fail(q.get(), st);
       }

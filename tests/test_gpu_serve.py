@@ -168,3 +168,43 @@ def test_server_k_lowest_states_match_oracle_and_are_mix_invariant(env, prec):
         assert ed.ed_server_get_stats(srv).failed == 0
     finally:
         ed.ed_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_server_packs_small_requests(env, prec):
+    """Requests whose sector has at most pack_dim states are solved in packs
+    (one batched Lanczos over all their sectors per step, Ritz vectors from the
+    stored basis, then each G).  Energies and G against the oracle; a request
+    alone (a pack of one) and in a pack of six with other models, k = 1 and
+    k = 4 requests in separate packs, and an unpacked larger request at the
+    same time, bit for bit."""
+    ed, ctx, torch = env
+    beta, nw, depth = 40.0, 128, 50
+    e_tol, g_tol = SERVE_TOL[prec]
+    small = [(W.kanamori(ns, seed=200 + i), (ns + 1) // 2, ns // 2) for i, ns in enumerate((8, 9, 10, 11, 9, 10))]
+    big = (W.kanamori(12, seed=300), 6, 6)                        # 853,776 states: not packed
+    srv = ed.ed_server_create(ctx, max_active=4, prec=prec, tol=LZ_TOL[prec], max_iter=3000, cf_depth=depth,
+                              n_w=nw, beta=beta, pack_dim=250_000)
+    try:
+        t_alone = ed.ed_submit(srv, *small[3], k=4)
+        alone = wait_all(ed, srv, [t_alone])[t_alone]
+        t_big = ed.ed_submit(srv, *big, k=1)
+        ts = [ed.ed_submit(srv, m, nu, nd, k=(4 if i < 4 else 1)) for i, (m, nu, nd) in enumerate(small)]
+        res = wait_all(ed, srv, ts + [t_big])
+        mix = res[ts[3]]
+        assert alone[0] == 0 and mix[0] == 0
+        assert alone[1] == mix[1] and np.array_equal(alone[3], mix[3])
+        assert _poll_energies[t_alone][1].E[:4] == _poll_energies[ts[3]][1].E[:4]
+        for i, ((m, nu, nd), t) in enumerate(zip(small + [big], ts + [t_big])):
+            st, E0, iters, G, lat = res[t]
+            assert st == 0, (i, st)
+            kk = 4 if i < 4 else 1
+            H = osec.build_csr(m, nu, nd)
+            w, v = spectrum.lowest(H, kk, vectors=True)
+            E = np.array(_poll_energies[t][1].E[:kk])
+            assert np.max(np.abs(E - w) / np.abs(w)) <= e_tol, (m.n_s, E, w)
+            Gref = og.greens_cf(m, [(nu, nd, w[j], v[:, j]) for j in range(kk)], beta, nw, m.orb0, 0, depth=depth)
+            assert np.max(np.abs(G - Gref)) <= g_tol, (m.n_s, np.max(np.abs(G - Gref)))
+        assert ed.ed_server_get_stats(srv).failed == 0
+    finally:
+        ed.ed_server_destroy(srv)
