@@ -429,21 +429,25 @@ def run_ours(a):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ed.ed_apply_h_host(sec, n_e2e, hx, hy, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / n_e2e
+    e2e_runs = []
+    for _ in range(3):   # the host link is shared with the machine's other tenants: median of three calls
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ed.ed_apply_h_host(sec, n_e2e, hx, hy, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_runs.append(e0.elapsed_time(e1) / n_e2e)
+    e2e_ms = statistics.median(e2e_runs)
     del hx, hy
     ms_step, e2e_ms = ranks_max([ms_step, e2e_ms], dist, "cuda")
     value = whole_job_gbs(world, nbytes, ms_step)
     e2e = {"value": whole_job_gbs(world, nbytes, e2e_ms), "unit": "GB/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": n_e2e,
-           "what": "one ed_apply_h_host C-ABI call on e2e_steps vectors in pinned host memory: every step's x "
-                   "copied host -> device and y device -> host inside the call, pipelined on the library's "
-                   "internal streams with the applies"}
+           "ms_per_step_runs": [round(v, 4) for v in e2e_runs],
+           "what": "ed_apply_h_host C-ABI calls on e2e_steps vectors in pinned host memory (median of three "
+                   "calls): every step's x copied host -> device and y device -> host inside the call, pipelined "
+                   "on the library's internal streams with the applies"}
 
     extras = {}
     if not a.no_extras and rank == 0:
