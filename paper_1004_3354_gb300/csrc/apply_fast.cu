@@ -1068,7 +1068,8 @@ void fast_variant_info(int prec, int v, int* kernel, int* block, int* min_blocks
 
 bool fast_variant_applies(const Sector* s, int v) {
   if (!s->fast.ok || v < 0 || v >= fast_variants()) return false;
-  if (v >= kNatBase) return s->fast.nat_ok;
+  if (v >= kNatBase)  // the rows a block stages must fit its shared memory
+    return s->fast.nat_ok && nat_variant_smem(s, v - kNatBase) + 1024 <= s->ctx->smem_optin;
   // float sectors with natural-order tables keep its float sums whatever the tuning
   if (s->fast.nat_ok && s->prec == ED_PREC_FP32) return false;
   return v < kNShapes || s->fast.pair_ok;
@@ -1081,7 +1082,12 @@ bool fast_variant_applies(const Sector* s, int v) {
 // memory, else 384 x 2 (24 warps either way; measured at N_s = 16, where
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
-  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) return kNatBase + 3;  // two rows, 256 x 3 (0.349 ms at N_s = 15)
+  if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
+    // two rows per block: 256 x 3 where three blocks fit an SM (0.349 ms at
+    // N_s = 15), else 512 x 2 (N_s = 16: 1.60 ms against 2.63 ms for 256 x 2)
+    const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
+    return kNatBase + (3 * (nat_variant_smem(s, 3) + 1024) <= per_sm ? 3 : 4);
+  }
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;
   const uint32_t D = s->dn.D;
   const int nc = s->fast.n_coef;
