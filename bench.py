@@ -792,6 +792,8 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
             out[f"served_{prec}_{mode}"] = {
                 "solves_per_s": n_req / el, "seconds": el, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "failed": stats.failed,
+                "server_stats_ms": {"latency_p50": stats.latency_p50_ms, "latency_p99": stats.latency_p99_ms,
+                                    "queue_p50": stats.queue_p50_ms, "queue_p99": stats.queue_p99_ms},
                 "not_converged": sum(1 for q in results if results[q]["status"] == ed.ED_ERR_NOT_CONVERGED),
                 "errors": sorted({f"{stream[q]['n_s']}: {results[q]['status']} {results[q]['error']}"
                                   for q in results if results[q]["status"] != 0})[:8],

@@ -55,7 +55,7 @@
 extern "C" {
 #endif
 
-#define ED_ABI_VERSION 2
+#define ED_ABI_VERSION 3
 
 typedef enum ed_status {
   ED_OK = 0,
@@ -508,8 +508,18 @@ typedef struct ed_result {
 } ed_result;
 
 typedef struct ed_server_stats {
-  int queued, active, done, failed, max_active_seen;
+  int queued;               /* submitted, not yet admitted (the queue depth) */
+  int active;               /* admitted, not yet finished */
+  int done, failed;         /* finished with ED_OK / with an error */
+  int max_active_seen;
   size_t bytes_in_flight;   /* estimated footprint of the admitted requests */
+  /* Over every finished request (done or failed, polled or not): the number
+   * of them, and the 50th / 99th percentiles of submission-to-completion
+   * (latency) and submission-to-admission (queue) times in ms, interpolated
+   * linearly between order statistics; 0 before the first one finishes. */
+  int n_latency;
+  double latency_p50_ms, latency_p99_ms;
+  double queue_p50_ms, queue_p99_ms;
 } ed_server_stats;
 
 /* Start a server on the context's device.  ED_ERR_INVALID on bad options. */

@@ -97,7 +97,7 @@ class ed_server_opts(C.Structure):
 
 
 ED_SERVE_MAX_K = 16
-ABI_VERSION = 2   # ED_ABI_VERSION of include/ed.h that these structures follow
+ABI_VERSION = 3   # ED_ABI_VERSION of include/ed.h that these structures follow
 
 
 class ed_request(C.Structure):
@@ -112,7 +112,9 @@ class ed_result(C.Structure):
 
 class ed_server_stats(C.Structure):
     _fields_ = [("queued", C.c_int), ("active", C.c_int), ("done", C.c_int), ("failed", C.c_int),
-                ("max_active_seen", C.c_int), ("bytes_in_flight", C.c_size_t)]
+                ("max_active_seen", C.c_int), ("bytes_in_flight", C.c_size_t), ("n_latency", C.c_int),
+                ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double),
+                ("queue_p50_ms", C.c_double), ("queue_p99_ms", C.c_double)]
 
 
 class ed_state(C.Structure):

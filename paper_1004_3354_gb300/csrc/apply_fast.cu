@@ -1075,17 +1075,22 @@ bool fast_variant_applies(const Sector* s, int v) {
   return v < kNShapes || s->fast.pair_ok;
 }
 
-// Untuned choice: the natural-order kernel for float sectors that have it (two
-// rows per block, 256 threads, three blocks per SM where they fit);
+// Untuned choice: the natural-order kernel for float sectors that have it
+// (four or two rows per block, by what the SM's shared memory holds);
 // otherwise two rows per block for float vectors, one otherwise; 256
 // threads x 3 blocks per SM while three staged blocks fit the SM's shared
 // memory, else 384 x 2 (24 warps either way; measured at N_s = 16, where
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
   if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
-    // two rows per block: 256 x 3 where three blocks fit an SM (0.349 ms at
-    // N_s = 15), else 512 x 2 (N_s = 16: 1.60 ms against 2.63 ms for 256 x 2)
+    // four rows per block, 384 x 2, where two such blocks fit an SM and the
+    // rows give every SM two blocks (N_s = 15: 0.309 ms against 0.338 ms for
+    // two rows, 256 x 3); else two rows, 256 x 3 where three blocks fit, else
+    // 512 x 2 (N_s = 16: 1.57 ms against 1.93 ms for four rows, 2.41 ms for
+    // two rows at 256 x 2)
     const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
+    const uint32_t sms = s->ctx->num_sms > 0 ? (uint32_t)s->ctx->num_sms : 152u;
+    if (2 * (nat_variant_smem(s, 2) + 1024) <= per_sm && (s->up.D + 3) / 4 >= 2 * sms) return kNatBase + 2;
     return kNatBase + (3 * (nat_variant_smem(s, 3) + 1024) <= per_sm ? 3 : 4);
   }
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;

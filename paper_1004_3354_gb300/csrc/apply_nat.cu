@@ -85,7 +85,7 @@ struct NatView {
   uint32_t D_up, D, n_grp, max_cnt;
   const uint32_t* row_order;
   const uint32_t* row_pat;      // diagonal pattern of each up string
-  const uint32_t* hop;          // [n_grp][max_cnt][32]: target rank << 8 | coefficient id
+  const uint32_t* hop;          // [n_grp][max_cnt/2][32][2]: target rank << 8 | coefficient id (max_cnt even)
   const uint32_t* meta;         // [n_grp*32]: hop count | diagonal pattern << 8 | impurity pattern << 16
   const void* coef;             // [n_coef] down-hop coefficients (float or double-float)
   int n_coef;
@@ -334,28 +334,31 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
       };
       gather(0);
       // pass A: down hops of the staged rows, padded to the group's longest
-      // list; hop words four at a time, the next four loaded ahead
+      // list; hop words four at a time (two 8-byte loads: a string's hops 2j
+      // and 2j + 1 sit side by side), the next four loaded ahead
       {
         const int gm = (int)__reduce_max_sync(0xffffffffu, (unsigned)cnt);
-        const uint32_t* hp = F.hop + (size_t)g * F.max_cnt * 32 + lane;
-        uint32_t h[4];
+        const uint2* hp = reinterpret_cast<const uint2*>(F.hop) + (size_t)g * (F.max_cnt / 2) * 32 + lane;
+        uint2 h[2];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) h[i] = i < gm ? __ldg(hp + (size_t)i * 32) : 0u;
+        for (int i = 0; i < 2; ++i) h[i] = 2 * i < gm ? __ldg(hp + (size_t)i * 32) : make_uint2(0u, 0u);
         for (int k = 0; k < gm; k += 4) {
-          uint32_t hn[4];
+          uint2 hn[2];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) hn[i] = k + 4 + i < gm ? __ldg(hp + (size_t)(k + 4 + i) * 32) : 0u;
+          for (int i = 0; i < 2; ++i)
+            hn[i] = k + 4 + 2 * i < gm ? __ldg(hp + (size_t)((k + 4) / 2 + i) * 32) : make_uint2(0u, 0u);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             if (k + i < gm) {
-              const C c = cs[h[i] & 255u];
-              const XV X = xs[h[i] >> 8];
+              const uint32_t wd = (i & 1) ? h[i >> 1].y : h[i >> 1].x;
+              const C c = cs[wd & 255u];
+              const XV X = xs[wd >> 8];
 #pragma unroll
               for (int r = 0; r < R; ++r) P::mac(Aa[r], c, X.v[r]);
             }
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) h[i] = hn[i];
+          for (int i = 0; i < 2; ++i) h[i] = hn[i];
         }
       }
       // pass B: CH steps per round trip
@@ -405,7 +408,7 @@ __global__ void k_nat_tables(uint32_t D, uint32_t n_grp, uint32_t max_cnt, const
   const uint32_t g = d / 32, lane = d % 32;
   const bool real = d < D;
   const uint32_t h0 = real ? dh_ptr[d] : 0u, c = real ? dh_ptr[d + 1] - h0 : 0u;
-  for (uint32_t k = 0; k < max_cnt; ++k) {
+  for (uint32_t k = 0; k < max_cnt; ++k) {  // max_cnt even: hops 2j, 2j + 1 side by side
     uint32_t word = (uint32_t)zero_id;  // staged element 0 times the zero coefficient
     if (k < c) {
       const double v = dh_val[h0 + k];
@@ -413,7 +416,7 @@ __global__ void k_nat_tables(uint32_t D, uint32_t n_grp, uint32_t max_cnt, const
       while (id < n_coef && coef[id] != v) ++id;
       word = (dh_tgt[h0 + k] << 8) | (uint32_t)id;
     }
-    hop[((size_t)g * max_cnt + k) * 32 + lane] = word;
+    hop[(((size_t)g * (max_cnt / 2) + k / 2) * 32 + lane) * 2 + (k & 1)] = word;
   }
   const uint32_t s = real ? dbasis[d] : 0u;
   const uint32_t pd = (real && wbits > 0) ? ((s >> w_lo) & ((1u << wbits) - 1u)) : 0u;
@@ -444,7 +447,7 @@ NatView make_nat_view(const Sector* s) {
   F.D_up = s->up.D;
   F.D = s->dn.D;
   F.n_grp = f.nat_grp;
-  F.max_cnt = f.max_cnt;
+  F.max_cnt = f.nat_mc;
   F.row_order = f.row_order;
   F.row_pat = f.row_pat;
   F.hop = f.nat_hop;
@@ -559,8 +562,9 @@ int build_nat(Sector* s, const std::vector<double>& coef, int zero_id) {
     return ED_OK;
   const uint32_t n_grp = (D + 31) / 32;
   f.nat_grp = n_grp;
+  f.nat_mc = (f.max_cnt + 1) & ~1u;
   const uint64_t NE = (uint64_t)n_grp * 32;
-  ED_TRY(sector_alloc(s, &f.nat_hop, (size_t)f.max_cnt * NE));
+  ED_TRY(sector_alloc(s, &f.nat_hop, (size_t)f.nat_mc * NE));
   ED_TRY(sector_alloc(s, &f.nat_meta, NE));
   ED_TRY(sector_alloc(s, &f.nat_edn, NE));
   ED_TRY(sector_alloc(s, &f.nat_coef, coef.size()));
@@ -569,7 +573,7 @@ int build_nat(Sector* s, const std::vector<double>& coef, int zero_id) {
   const int wbits = (s->n_chunks == 1) ? s->w_bits[0] : 0;
   const double* W = (s->n_chunks == 1) ? s->W : nullptr;
   k_nat_tables<<<(unsigned)((NE + 127) / 128), 128>>>(
-      D, n_grp, f.max_cnt, s->dn.basis, s->dn.hop_ptr, s->dn.hop_tgt, s->dn.hop_val, f.coef, (int)coef.size(), zero_id,
+      D, n_grp, f.nat_mc, s->dn.basis, s->dn.hop_ptr, s->dn.hop_tgt, s->dn.hop_val, f.coef, (int)coef.size(), zero_id,
       s->dn.e, W, s->w_lo, wbits, s->orb0, f.mix_delta ? s->M : 0, f.nat_hop, f.nat_meta, f.nat_edn,
       s->prec == ED_PREC_DF64 ? f.nat_dd : nullptr);
   ED_LAUNCH_CHECK();

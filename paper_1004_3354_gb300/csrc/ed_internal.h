@@ -215,7 +215,8 @@ struct Sector {
     // owns down string 32 g + l, R up strings per block
     bool nat_ok = false;
     uint32_t nat_grp = 0;           // ceil(D_dn / 32)
-    uint32_t* nat_hop = nullptr;    // [nat_grp][max_cnt][32]: target rank << 8 | coefficient id
+    uint32_t nat_mc = 0;            // hop slots per string: max_cnt rounded up to even
+    uint32_t* nat_hop = nullptr;    // [nat_grp][nat_mc/2][32][2]: target rank << 8 | coefficient id
     uint32_t* nat_meta = nullptr;   // [nat_grp*32]: hop count | diagonal pattern << 8 | impurity pattern << 16
     float* nat_edn = nullptr;       // [nat_grp*32] e_dn as float
     float* nat_coef = nullptr;      // [n_coef] down-hop coefficients as float

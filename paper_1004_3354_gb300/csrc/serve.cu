@@ -276,6 +276,7 @@ struct Server : ServerBase {
   uint64_t next_ticket = 1;
   size_t in_flight_bytes = 0;
   int n_done = 0, n_failed = 0, max_active_seen = 0;
+  std::vector<double> lat_ms, wait_ms;  // per finished request: submission to completion / admission
 
   Server(Ctx* c, const ed_server_opts& op) : ctx(c), o(op) { th = std::thread([this] { loop(); }); }
   ~Server() override {
@@ -396,7 +397,23 @@ struct Server : ServerBase {
     s->failed = n_failed;
     s->bytes_in_flight = in_flight_bytes;
     s->max_active_seen = max_active_seen;
+    s->n_latency = (int)lat_ms.size();
+    s->latency_p50_ms = percentile(lat_ms, 50.0);
+    s->latency_p99_ms = percentile(lat_ms, 99.0);
+    s->queue_p50_ms = percentile(wait_ms, 50.0);
+    s->queue_p99_ms = percentile(wait_ms, 99.0);
     return ED_OK;
+  }
+
+  // q-th percentile with linear interpolation between order statistics
+  // (position q/100 * (n - 1) in the sorted values); 0 without values
+  static double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q / 100.0 * (double)(v.size() - 1);
+    const size_t i = (size_t)pos;
+    if (i + 1 >= v.size()) return v.back();
+    return v[i] + (pos - (double)i) * (v[i + 1] - v[i]);
   }
 
   void fail(Req<V>* q, int st) {
@@ -870,6 +887,8 @@ struct Server : ServerBase {
             in_flight_bytes -= std::min(in_flight_bytes, q->footprint);
             if (q->phase == PH_DONE && q->status == ED_OK) ++n_done;
             else ++n_failed;
+            lat_ms.push_back(q->t_done - q->t_submit);
+            wait_ms.push_back(q->t_admit - q->t_submit);
             q->release();
             finished[q->ticket] = std::move(active[i]);
             active.erase(active.begin() + i);

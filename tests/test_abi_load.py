@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_abi_version_and_error_path_without_gpu():
     ed = ensure_built()
-    assert ed.lib().ed_abi_version() == ed.ABI_VERSION == 2
+    assert ed.lib().ed_abi_version() == ed.ABI_VERSION == 3
     # NULL output handle is rejected before any device work
     st = ed.lib().ed_ctx_create(0, 0, None)
     assert st == ed.ED_ERR_INVALID

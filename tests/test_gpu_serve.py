@@ -117,6 +117,16 @@ def test_server_admission_budget_and_errors(env):
             time.sleep(0.001)
         res = wait_all(ed, srv, ts)
         assert all(r[0] == 0 for r in res.values())
+        # latency and queue-time percentiles over the finished requests, as
+        # numpy's linear interpolation of the times the results carry
+        st = ed.ed_server_get_stats(srv)
+        assert st.n_latency == len(ts) and st.queued == 0 and st.active == 0
+        lat = [_poll_energies[t][1].latency_ms for t in ts]
+        wait = [_poll_energies[t][1].queue_ms for t in ts]
+        for got, ref in ((st.latency_p50_ms, np.percentile(lat, 50)), (st.latency_p99_ms, np.percentile(lat, 99)),
+                         (st.queue_p50_ms, np.percentile(wait, 50)), (st.queue_p99_ms, np.percentile(wait, 99))):
+            assert abs(got - ref) <= 1e-9 * max(1.0, abs(ref)), (got, ref)
+        assert 0 < st.latency_p50_ms <= st.latency_p99_ms <= max(lat)
         # a request larger than the whole budget is refused at submission
         big = W.kanamori(16, seed=1)
         with pytest.raises(ed.EdError) as e:
