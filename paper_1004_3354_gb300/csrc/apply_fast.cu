@@ -1083,14 +1083,14 @@ bool fast_variant_applies(const Sector* s, int v) {
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
   if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
-    // four rows per block, 384 x 2, where two such blocks fit an SM and the
-    // rows give every SM two blocks (N_s = 15: 0.309 ms against 0.338 ms for
+    // four rows per block, 512 x 2, where two such blocks fit an SM and the
+    // rows give every SM two blocks (N_s = 15: 0.279 ms against 0.349 ms for
     // two rows, 256 x 3); else two rows, 256 x 3 where three blocks fit, else
-    // 512 x 2 (N_s = 16: 1.57 ms against 1.93 ms for four rows, 2.41 ms for
-    // two rows at 256 x 2)
+    // 512 x 2 (N_s = 16: 1.57 ms against 1.77 ms for four rows, one block
+    // per SM)
     const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
     const uint32_t sms = s->ctx->num_sms > 0 ? (uint32_t)s->ctx->num_sms : 152u;
-    if (2 * (nat_variant_smem(s, 2) + 1024) <= per_sm && (s->up.D + 3) / 4 >= 2 * sms) return kNatBase + 2;
+    if (2 * (nat_variant_smem(s, 1) + 1024) <= per_sm && (s->up.D + 3) / 4 >= 2 * sms) return kNatBase + 1;
     return kNatBase + (3 * (nat_variant_smem(s, 3) + 1024) <= per_sm ? 3 : 4);
   }
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
       // pass B set-up: this string's pattern list, all R rows per step.  The
       // gathers of its first CH steps are issued now, so that their L2
       // latency overlaps the shared-memory work of the down hops.
-      constexpr int CH = kF32 ? 8 : 4;
+      constexpr int CH = kF32 ? 16 / R : 4;   // float: 16 gathers in flight per thread
       const int nl = ok ? lmx[ip] : 0;
       const int nmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)nl);
       const OV* Lo = reinterpret_cast<const OV*>(loff + (size_t)ip * lcap * R);
