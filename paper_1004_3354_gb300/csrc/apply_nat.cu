@@ -312,23 +312,42 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
       const CV* Lc = reinterpret_cast<const CV*>(lcf + (size_t)ip * lcap * R);
       const V* xd = x + d;
       V xc[CH][R];
+      // (a chunk whose CH steps all lie in this lane's list runs unguarded)
       auto gather = [&](int k0) {
+        if (k0 + CH <= nl) {
 #pragma unroll
-        for (int s = 0; s < CH; ++s) {
-          if (k0 + s < nl) {
+          for (int s = 0; s < CH; ++s) {
             const OV o = Lo[k0 + s];
 #pragma unroll
             for (int r = 0; r < R; ++r) xc[s][r] = __ldg(xd + o.v[r]);
           }
+        } else {
+#pragma unroll
+          for (int s = 0; s < CH; ++s) {
+            if (k0 + s < nl) {
+              const OV o = Lo[k0 + s];
+#pragma unroll
+              for (int r = 0; r < R; ++r) xc[s][r] = __ldg(xd + o.v[r]);
+            }
+          }
         }
       };
       auto add = [&](int k0) {
+        if (k0 + CH <= nl) {
 #pragma unroll
-        for (int s = 0; s < CH; ++s) {
-          if (k0 + s < nl) {
+          for (int s = 0; s < CH; ++s) {
             const CV c = Lc[k0 + s];
 #pragma unroll
             for (int r = 0; r < R; ++r) P::mac(Bb[r], c.v[r], xc[s][r]);
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < CH; ++s) {
+            if (k0 + s < nl) {
+              const CV c = Lc[k0 + s];
+#pragma unroll
+              for (int r = 0; r < R; ++r) P::mac(Bb[r], c.v[r], xc[s][r]);
+            }
           }
         }
       };
