@@ -375,12 +375,13 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_win(FastView F, const typena
 // Two up strings per block: rows A and B share every down hop (same hop word,
 // same coefficient, same staged offset), so the two rows are staged
 // interleaved ({A, B} per rank for floats, {A.hi, B.hi, A.lo, B.lo} for
-// double-float), the coefficients are kept as {hi, hi, lo, lo}, and one f32x2
-// instruction advances both rows' double-float accumulators.  Hop words,
-// window permutation and coefficient loads are shared by the two rows.  It is
-// the default for float vectors; for double-float rows (16 bytes per rank) two
-// blocks leave the SM little L1 and the single-row kernel is usually faster,
-// which the autotuner measures per sector.
+// double-float), the coefficients are kept as {hi, hi, lo, lo}, and both rows'
+// double-float accumulators advance together (f32x2 instructions for float
+// rows, scalar ones for double-float rows).  Hop words, window permutation and
+// coefficient loads are shared by the two rows.  It is the default for float
+// vectors with double-float sums; for double-float rows (16 bytes per rank)
+// two blocks leave the SM little L1 and the single-row kernel is usually
+// faster, which the autotuner measures per sector.
 __device__ __forceinline__ void cp_async4(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g));
@@ -429,6 +430,23 @@ template <class P>
 size_t pair_smem(uint32_t D, int n_coef) {
   return align16(D * sizeof(typename PairTraits<P>::PV)) + align16((size_t)n_coef * 16) + 4 * align16(kList * 16) +
          align16(kList * 8) + align16(kMaxDelta * 4);
+}
+
+// The two rows' multiply-adds of a pair, lane-wise exactly df_mac (XLO, x in
+// double-float) or df_mac1 (float x).  Double-float rows run them as scalar
+// FP32 instructions (0.70 ms against 0.78 ms with f32x2 at N_s = 15), float
+// rows as f32x2 instructions (0.49 ms against 0.55 ms scalar).
+template <bool XLO>
+__device__ __forceinline__ void df_mac2s(float2& H, float2& L, float2 Ch, float2 Cl, float2 Xh, float2 Xl) {
+  if (XLO) {
+    float2 a = make_float2(H.x, L.x), b = make_float2(H.y, L.y);
+    df_mac(a, make_float2(Ch.x, Cl.x), make_float2(Xh.x, Xl.x));
+    df_mac(b, make_float2(Ch.y, Cl.y), make_float2(Xh.y, Xl.y));
+    H = make_float2(a.x, b.x);
+    L = make_float2(a.y, b.y);
+  } else {
+    df_mac2<false>(H, L, Ch, Cl, Xh, Xl);
+  }
 }
 
 // coefficient pair (sa * c_A, sb * c_B) from a {A.hi, B.hi, A.lo, B.lo} entry, sa, sb in {0, 1, -1}
@@ -555,9 +573,9 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typen
       for (int e = 0; e < 4; ++e) {
         const PV X = xs[dv[e]];
         H[e] = L[e] = make_float2(0.f, 0.f);
-        df_mac2<XLO>(H[e], L[e], make_float2(dga[e].x, dgb[e].x), make_float2(dga[e].y, dgb[e].y), T::hi(X),
+        df_mac2s<XLO>(H[e], L[e], make_float2(dga[e].x, dgb[e].x), make_float2(dga[e].y, dgb[e].y), T::hi(X),
                      T::lo(X));
-        df_mac2<XLO>(H[e], L[e], EUh, EUl, T::hi(X), T::lo(X));
+        df_mac2s<XLO>(H[e], L[e], EUh, EUl, T::hi(X), T::lo(X));
       }
       // down hops: slot counts descend (c0 >= c1 >= c2 >= c3)
       {
@@ -569,7 +587,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typen
   do {                                                                                                     \
     const float4 cc = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(cs) + ((WD) & 0x1fffu)); \
     const PV X = *reinterpret_cast<const PV*>(reinterpret_cast<const unsigned char*>(xs) + ((WD) >> 13));  \
-    df_mac2<XLO>(H[E], L[E], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi(X), T::lo(X));        \
+    df_mac2s<XLO>(H[E], L[E], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi(X), T::lo(X));        \
   } while (0)
         for (; k < c3; ++k) {
           const uint4 h = __ldg(hp + (uint64_t)k * 32);
@@ -601,7 +619,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typen
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
+          df_mac2s<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
                        T::lo2(a[e], b[e]));
       }
       // spin-flip / pair-hop
@@ -626,7 +644,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typen
             }
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-              df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
+              df_mac2s<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a[e], b[e]),
                            T::lo2(a[e], b[e]));
           }
         } else {
@@ -661,7 +679,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_pair(FastView F, const typen
               if (mda == INT_MIN && mdb == INT_MIN) continue;
               const float4 cc = sign_pair(c0, mda, mdb);
               const V a = __ldg(x + ia), b = __ldg(x + ib);
-              df_mac2<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a, b),
+              df_mac2s<XLO>(H[e], L[e], make_float2(cc.x, cc.y), make_float2(cc.z, cc.w), T::hi2(a, b),
                            T::lo2(a, b));
             }
           }
