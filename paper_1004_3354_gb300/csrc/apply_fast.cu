@@ -1101,14 +1101,16 @@ bool fast_variant_applies(const Sector* s, int v) {
 // 384 x 2 beats 256 x 2 by ~20%).
 int fast_default_variant(const Sector* s) {
   if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
-    // four rows per block, 512 x 2, where two such blocks fit an SM and the
-    // rows give every SM two blocks (N_s = 15: 0.279 ms against 0.349 ms for
-    // two rows, 256 x 3); else two rows, 256 x 3 where three blocks fit, else
-    // 512 x 2 (N_s = 16: 1.57 ms against 1.77 ms for four rows, one block
-    // per SM)
+    // four rows per block and 32 warps per SM: 512 x 2 where two such blocks
+    // fit an SM (N_s = 15: 0.279 ms against 0.332 ms for two rows, 256 x 3),
+    // else 1024 x 1 where one fits (N_s = 16: 1.48 ms against 1.64 ms for two
+    // rows, 512 x 2), as long as the rows give every SM its blocks; else two
+    // rows, 256 x 3 where three blocks fit, else 512 x 2
     const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;
     const uint32_t sms = s->ctx->num_sms > 0 ? (uint32_t)s->ctx->num_sms : 152u;
-    if (2 * (nat_variant_smem(s, 1) + 1024) <= per_sm && (s->up.D + 3) / 4 >= 2 * sms) return kNatBase + 1;
+    const uint32_t tiles4 = (s->up.D + 3) / 4;
+    if (2 * (nat_variant_smem(s, 1) + 1024) <= per_sm && tiles4 >= 2 * sms) return kNatBase + 1;
+    if (nat_variant_smem(s, 0) + 1024 <= std::min(per_sm, s->ctx->smem_optin) && tiles4 >= sms) return kNatBase + 0;
     return kNatBase + (3 * (nat_variant_smem(s, 3) + 1024) <= per_sm ? 3 : 4);
   }
   const bool pair = s->prec == ED_PREC_FP32 && s->fast.pair_ok;

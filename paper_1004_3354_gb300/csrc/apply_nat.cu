@@ -516,8 +516,8 @@ int launch_nat_t(const Sector* s, const void* x, void* y, cudaStream_t st, doubl
 // Variants per format: rows per block R x threads per block x blocks per SM
 // the register budget is sized for (shared memory may allow fewer).
 constexpr int kNatR[2][kNatVariants] = {{4, 4, 4, 2, 2, 2}, {2, 2, 2, 1, 1, 1}};
-constexpr int kNatBS[2][kNatVariants] = {{256, 512, 384, 256, 512, 384}, {256, 512, 384, 256, 512, 384}};
-constexpr int kNatMinB[2][kNatVariants] = {{2, 2, 2, 3, 2, 2}, {2, 1, 2, 3, 2, 2}};
+constexpr int kNatBS[2][kNatVariants] = {{1024, 512, 384, 256, 512, 384}, {256, 512, 384, 256, 512, 384}};
+constexpr int kNatMinB[2][kNatVariants] = {{1, 2, 2, 3, 2, 2}, {2, 1, 2, 3, 2, 2}};
 
 int fmt_of(int prec) { return prec == ED_PREC_FP32 ? 0 : 1; }
 int fmt_of(const Sector* s) { return fmt_of(s->prec); }
@@ -541,7 +541,7 @@ int launch_nat(const Sector* s, int v, const void* x, void* y, cudaStream_t st, 
   if (!s->fast.nat_ok) ED_INVALID("the sector has no natural-order tables");
   if (s->prec == ED_PREC_FP32) {
     switch (v) {
-      case 0: return launch_nat_t<NatF32, 4, 256, 2>(s, x, y, st, dotp, nparts);
+      case 0: return launch_nat_t<NatF32, 4, 1024, 1>(s, x, y, st, dotp, nparts);
       case 1: return launch_nat_t<NatF32, 4, 512, 2>(s, x, y, st, dotp, nparts);
       case 2: return launch_nat_t<NatF32, 4, 384, 2>(s, x, y, st, dotp, nparts);
       case 3: return launch_nat_t<NatF32, 2, 256, 3>(s, x, y, st, dotp, nparts);
