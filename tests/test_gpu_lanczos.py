@@ -171,6 +171,24 @@ def test_c1_ground_state_three_vectors(env, prec):
         ed.ed_sector_destroy(sec)
 
 
+def test_c1_fp32_every_natural_order_variant(env):
+    """Each launch shape of the float natural-order kernel (four or two rows per
+    block, 256 to 1024 threads) inside the three-vector Lanczos step, where
+    H*v also returns its per-block parts of <q, Hq>: ground energy within 1e-6
+    relative of the oracle's."""
+    ed, ctx, torch = env
+    r = c1_reference()
+    sec = ed.ed_sector_create(ctx, r["m"], 6, 6, "fp32")
+    try:
+        for v in range(10, 16):
+            ed.ed_sector_set_variant(sec, v)
+            ev, info, st = ed.ed_lanczos(sec, k=1, tol=1e-7, max_iter=400, reorth=False, allow_not_converged=True)
+            assert ed.ed_sector_get_info(sec).kernel == 4
+            assert abs(ev[0] - r["e0"]) <= 1e-6 * abs(r["e0"]), (v, ev[0], r["e0"])
+    finally:
+        ed.ed_sector_destroy(sec)
+
+
 def test_c1_fp32_vectors_ground_energy(env):
     """FP32 Lanczos vectors, double-float products: ground energy within 1e-6 relative."""
     ed, ctx, torch = env
