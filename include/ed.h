@@ -418,14 +418,15 @@ int ed_batch_destroy(ed_batch* b);
  * every sector's start vector).  All active sectors advance together: each
  * step is one replay of a CUDA graph whose kernels (one H*v over all sectors,
  * dot products, update, CGS2, norm, scaling) each run as a single launch over a
- * device work list of (sector, 1024-element chunk) items; converged sectors
+ * device work list of (sector, chunk of elements) items; converged sectors
  * drop out of the list.  evals: host, n_sectors * k (NaN past a sector's
  * dimension); iters: host, n_sectors (may be NULL).  Synchronises. */
 int ed_batch_lanczos(ed_batch* b, const ed_lanczos_opts* opts, double* evals, int* iters,
                      ed_batch_info* info, void* stream);
 
 /* Sector packing of the batch: every sector is cut into work items of `chunk`
- * consecutive elements (1024 by default), and each batched kernel runs one
+ * consecutive elements (by default the largest power of two from 256 to 8192
+ * that gives at least eight items per SM), and each batched kernel runs one
  * launch over the item list.  ed_batch_set_chunk sets it (a power of two in
  * 64..65536; ED_ERR_INVALID otherwise).  ed_batch_autotune runs `steps`
  * graph-replayed Lanczos steps (2..64) of every sector with each candidate
