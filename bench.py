@@ -753,7 +753,7 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
         ed.ed_sector_destroy(sec)
         del vecs, states
         service.append(time.perf_counter() - t0)
-        base[q] = {"E": [float(e) for e in ev], "G": G, "status": st}
+        base[q] = {"E": [float(e) for e in ev], "G": G, "status": st, "iters": int(info.iters)}
     base_total = time.perf_counter() - t_all
     base_rate = n_req / base_total
     rate = 0.8 * base_rate                      # open-loop arrivals at 0.8x plain capacity
@@ -770,6 +770,8 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
                "poisson": {"p50_ms": float(np.percentile(lat_poi, 50)), "p99_ms": float(np.percentile(lat_poi, 99)),
                            "arrival_rate_per_s": rate},
                "not_converged": sum(1 for v in base.values() if v["status"] != 0),
+               "mean_iters": float(np.mean([v["iters"] for v in base.values()])),
+               "max_iters": max(v["iters"] for v in base.values()),
                **oracle_errors(base, golden, pts, k, stream)}}
     budget = 200 * 1024 ** 3
     for prec in list(precs) + (["fp64"] if served_fp64 else []):
@@ -808,6 +810,7 @@ def serve_bench(ed, ctx, torch, n_req=16, k=4, tol=1e-8, precs=("fp32",), modes=
                 "errors": sorted({f"{stream[q]['n_s']}: {results[q]['status']} {results[q]['error']}"
                                   for q in results if results[q]["status"] != 0})[:8],
                 "max_iters": max(results[q]["iters"] for q in results),
+                "mean_iters": float(np.mean([results[q]["iters"] for q in results])),
                 "max_active_seen": stats.max_active_seen, "arrival_rate_per_s": None if mode == "saturation" else rate,
                 "max_rel_E0_diff_vs_plain_fp64": e_vs_plain, **oracle_errors(results, golden, pts, k, stream)}
     if "served_fp32_saturation" in out:
