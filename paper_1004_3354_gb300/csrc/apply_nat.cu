@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
       const CV* Lc = reinterpret_cast<const CV*>(lcf + (size_t)ip * lcap * R);
       const V* xd = x + d;
       V xc[CH][R];
-      // (a chunk whose CH steps all lie in this lane's list runs unguarded)
+      // A chunk whose CH steps all lie in this lane's list runs without the
+      // per-step guards.
       auto gather = [&](int k0) {
         if (k0 + CH <= nl) {
 #pragma unroll

@@ -27,9 +27,9 @@ def env():
 
 # fast H*v variants: [0, 5) one up string per block (kernel 2), [5, 10) two up
 # strings per block (kernel 3), both x five launch shapes; [10, 16) the
-# natural-order kernel (kernel 4) for float and double-float vectors, two or
-# four (float) / one or two (double-float) up strings per block x three block
-# sizes
+# natural-order kernel (kernel 4) for float and double-float vectors, four or
+# two (float) / two or one (double-float) up strings per block x three block
+# sizes (float four-row blocks of 1024, 512 and 384 threads)
 NV = 16
 KERNELS = [2] * 5 + [3] * 5 + [4] * 6
 
