@@ -265,7 +265,8 @@ typedef struct ed_tune_result {
   int n_candidates;               /* variants tried, in the order of the arrays */
   int chosen;                     /* index of the fastest, now the sector's H*v; -1: nothing to choose */
   int kernel[ED_MAX_TUNE];        /* 2: one up string per block, 3: two up strings per block,
-                                     4: natural-order float kernel, two or four up strings per block */
+                                     4: natural-order kernel, four or two (float) / two or one
+                                     (double-float) up strings per block */
   int block[ED_MAX_TUNE];         /* threads per block */
   int min_blocks[ED_MAX_TUNE];    /* blocks per SM the register budget is sized for */
   double ms[ED_MAX_TUNE];         /* median device time of one H*v; -1 where it does not apply or fit */
@@ -273,12 +274,15 @@ typedef struct ed_tune_result {
 
 /* Autotuner of the matrix-free H*v (the hot loop of Sec. 3's iterative
  * solvers; the paper has no tuner): times every variant of the fast row
- * kernel that applies to this sector -- one or two up strings per block, times
- * the launch shapes (threads per block, blocks per SM) -- `reps` times each
+ * kernels that applies to this sector -- one, two or four up strings per block,
+ * times the launch shapes (threads per block, blocks per SM) -- `reps` times each
  * (median, CUDA events, after a warm-up) on internal random vectors, makes the
  * fastest the sector's H*v, and records it in the context's cache under the
  * sector's shape (format, sizes, hop counts), so that sectors of the same shape
- * created later start with it.  All variants compute the same y bit for bit.
+ * created later start with it.  The variants of one kernel compute the same y
+ * bit for bit; for double-float vectors the kernels (kernel ids 2, 3, 4) sum in
+ * different orders and agree to rounding; float sectors that have the
+ * natural-order kernel are tuned among its variants only.
  * Sectors without the fast kernel (ED_SECTOR_GENERIC, very short rows) have
  * nothing to tune: n_candidates = 0, chosen = -1.  Allocates two vectors for
  * the duration of the call.  Synchronises. */
