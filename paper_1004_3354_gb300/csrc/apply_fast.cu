@@ -1103,7 +1103,7 @@ int fast_default_variant(const Sector* s) {
   if (s->fast.nat_ok && s->prec == ED_PREC_FP32) {
     // four rows per block and 32 warps per SM: 512 x 2 where two such blocks
     // fit an SM (N_s = 15: 0.279 ms against 0.332 ms for two rows, 256 x 3),
-    // else 1024 x 1 where one fits (N_s = 16: 1.48 ms against 1.64 ms for two
+    // else 1024 x 1 where one fits (N_s = 16: 1.31 ms against 1.63 ms for two
     // rows, 512 x 2), as long as the rows give every SM its blocks; else two
     // rows, 256 x 3 where three blocks fit, else 512 x 2
     const size_t per_sm = s->ctx->smem_per_sm ? s->ctx->smem_per_sm : 228 * 1024;

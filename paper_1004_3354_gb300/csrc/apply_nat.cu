@@ -166,6 +166,8 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
   int* pus = reinterpret_cast<int*>(p);           // diagonal pattern of each row
   int* urs = pus + R;                             // element offset u * D of each row
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr bool kDyn = MINB == 1;   // one block per SM: groups handed out on demand
+  __shared__ uint32_t gnext;          // next group of the tile not yet taken
 
   const C* gcoef = static_cast<const C*>(F.coef);
   for (int k = threadIdx.x; k < F.n_coef; k += BS) cs[k] = gcoef[k];
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
   const uint32_t n_tiles = (F.D_up + R - 1) / R;
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     __syncthreads();  // the previous tile is done with the staged rows and lists
+    if (kDyn && threadIdx.x == 0) gnext = NWARP;   // groups past the warps' first ones go on demand
     {
       const V* xr[R];
 #pragma unroll
@@ -275,7 +278,21 @@ __global__ void __launch_bounds__(BS, MINB) k_apply_nat(NatView F, const typenam
     cp_async_all();
     __syncthreads();
 
-    for (uint32_t g = warp; g < F.n_grp; g += NWARP) {
+    // With one block per SM each warp takes group `warp` first, then the next
+    // untaken one, so the warps end a tile together however the groups' costs
+    // vary (N_s = 16, four rows, 1024 x 1: 1.29 ms against 1.50 ms with every
+    // NWARP-th group); with two blocks per SM the other block fills the tail
+    // of a tile and the fixed order reads neighbouring groups together.
+    auto next_group = [&](uint32_t g) {
+      if constexpr (!kDyn) {
+        return g + NWARP;
+      } else {
+        uint32_t nx = 0;
+        if (lane == 0) nx = atomicAdd(&gnext, 1u);
+        return __shfl_sync(0xffffffffu, nx, 0);
+      }
+    };
+    for (uint32_t g = warp; g < F.n_grp; g = next_group(g)) {
       const uint32_t d = g * 32 + lane;
       const bool ok = d < D;
       const uint32_t mt = __ldg(F.meta + d);   // padding entries: count 0, patterns 0
