@@ -39,9 +39,16 @@
  *                    kernel) sums each element in float in two passes
  *                    (diagonal and down hops; up hops, spin-flip and pair-hop)
  *                    with coefficients rounded to float and adds the two
- *                    partial sums with one rounding: an element with n terms
- *                    is within about (n + 3) 2^-24 sum_j |H_ij x_j| of the
- *                    exact value.  The other H*v kernels (general models) form
+ *                    partial sums with one rounding: to first order in
+ *                    u = 2^-24, |y_i - (Hx)_i| <= u [(n_A + 1) sum_A |H_ij x_j|
+ *                    + 4 S_i |x_i| + (n_B + 1) sum_B |H_ij x_j| + |(Hx)_i|],
+ *                    with sum_A over the n_A entries of the row's own up string
+ *                    (diagonal and down hops), sum_B over the n_B others and
+ *                    S_i the summed magnitude of the density terms (T_ii, U,
+ *                    U', U' - J) present in state i, from which the diagonal
+ *                    is formed (tested element by element; about (n + 3) u
+ *                    sum_j |H_ij x_j| for n terms when the diagonal does not
+ *                    cancel).  The other H*v kernels (general models) form
  *                    every product and sum in double-float and round once.
  *                    Dot products and norms accumulate in double-float.
  */

@@ -20,10 +20,11 @@
 //      B = sum over up hops, spin-flip, pair-hop (other rows, from L2)
 //    and y = A + B rounded once.
 //      float vectors: A and B are float sums (one FMA per term) with the
-//        coefficients and the diagonal rounded to float, y = fl(A + B); with
-//        u = 2^-24 and n_A, n_B terms, |y - (Hx)_i| <= (n_A + 3) u
-//        sum_A |H_ij x_j| + (n_B + 1) u sum_B |H_ij x_j| + u |(Hx)_i| to first
-//        order.
+//        coefficients rounded to float and the diagonal formed in float from
+//        three float pieces (e_up + e_dn + W), y = fl(A + B); with u = 2^-24,
+//        n_A and n_B terms and S_i the summed magnitude of the density terms
+//        behind the diagonal, |y - (Hx)_i| <= u [(n_A + 1) sum_A |H_ij x_j| +
+//        4 S_i |x_i| + (n_B + 1) sum_B |H_ij x_j| + |(Hx)_i|] to first order.
 //      double-float vectors: every product and sum in double-float (Dekker /
 //        Knuth error-free transformations, about 2^-46 relative), A + B
 //        normalised once.

@@ -6,17 +6,19 @@ The natural-order float kernel sums each element in float in two passes
 (diagonal + down hops, then up hops + spin-flip / pair-hop) with the
 coefficients rounded to float, so an element's error is at most about
 (n + 3) 2^-24 sum_j |H_ij x_j| for n terms (~1e-6 relative for 15 terms in the
-worst case, ~1e-7 typical); the double-float-accumulating kernels (the
-fallback) round once.  The test allows 1e-6 norm-wise.
+worst case, ~1e-7 typical; the exact first-order bound is checked element by
+element below); the double-float-accumulating kernels (the fallback) round
+once.  The norm-wise tests allow 1e-6.
 Small sectors are checked element by element on every row; large ones (row
 lengths that select the row-staged kernel, and the full N_s=15 half-filled
 sector the benchmark times) on sampled rows, first/last/ragged rows included.
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import workloads as W
-from oracle import sector as osec
+from oracle import fock, sector as osec
 from tests._gpu import ensure_built, torch_cuda, to_dev, to_host, empty_vec, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -276,6 +278,60 @@ def test_apply_host_buffers_pipeline(env, prec):
             ed.ed_apply_h_host(sec, 1, None, hy1)
     finally:
         ed.ed_sector_destroy(sec)
+
+
+def density_term_magnitude(m, nu, nd):
+    """Per basis state, the sum of |coefficient| over the density terms of H that
+    are on in it (T_ii n_is, U_i n_iu n_id, (U' - J delta_ss') n_ms n_m's'): a
+    bound on |e_up| + |e_dn| + |W|, the three pieces the float kernel rounds to
+    float and adds to form the diagonal (e_up of the up string, e_dn of the down
+    string, W of their orbital occupations)."""
+    def density(ops):
+        return all(ops[k][0] == ops[k + 1][0] and ops[k][1] and not ops[k + 1][1] for k in range(0, len(ops), 2))
+    terms = [(abs(c), ops) for c, ops in fock.hamiltonian_terms(m) if density(ops)]
+    return osec.build_csr(m, nu, nd, terms=terms).diagonal()
+
+
+ELEMENTWISE = [("Kanamori N_s=12 (6,6)", lambda: W.kanamori(12, seed=0), 6, 6),
+               ("Kanamori N_s=13 (6,7)", lambda: W.kanamori(13, seed=3), 6, 7),
+               ("AIM N_s=12 (6,6)", lambda: W.aim(12, seed=2), 6, 6)]
+
+
+@pytest.mark.parametrize("name,mk,nu,nd", ELEMENTWISE, ids=[c[0] for c in ELEMENTWISE])
+def test_fp32_float_sums_within_elementwise_bound(env, name, mk, nu, nd):
+    """The natural-order float kernel's error, element by element, against the
+    first-order bound of its arithmetic: pass A (diagonal, then n_A - 1 down
+    hops) and pass B (n_B up hops and spin-flip / pair-hop terms) are FMA chains
+    in float with the coefficients rounded to float (one rounding each), the
+    diagonal is formed from three float pieces by two additions and multiplies
+    x_i once, and y = fl(A + B):
+      |y_i - (Hx)_i| <= u [(n_A + 1) sum_A |H_ij x_j| + 4 S_i |x_i|
+                           + (n_B + 1) sum_B |H_ij x_j| + |(Hx)_i|],
+    u = 2^-24, sum_A over the row's own up string, sum_B over the others, S_i
+    the density-term magnitude of state i, with a 1% allowance for second-order
+    terms."""
+    ed, ctx, torch = env
+    m = mk()
+    H = oracle_csr(name, m, nu, nd)
+    n = H.shape[0]
+    D_dn = len(osec.spin_basis(m.n_s, nd))
+    x = input_for("fp32", W.random_vector(n, seed=7))
+    ref = H @ x
+    y = run_apply(ed, ctx, torch, m, nu, nd, "fp32", x, expect_kernel=4)
+    coo = H.tocoo()
+    own = (coo.row // D_dn) == (coo.col // D_dn)
+    A = sp.csr_matrix((np.abs(coo.data[own]), (coo.row[own], coo.col[own])), shape=H.shape)
+    B = sp.csr_matrix((np.abs(coo.data[~own]), (coo.row[~own], coo.col[~own])), shape=H.shape)
+    n_A = np.diff(A.indptr) + 1          # entries of the row (diagonal included), plus one for duplicates
+    n_B = np.diff(B.indptr) + 1
+    S = density_term_magnitude(m, nu, nd)
+    ax = np.abs(x)
+    u = 2.0 ** -24
+    bound = u * ((n_A + 1) * (A @ ax) + 4 * S * ax + (n_B + 1) * (B @ ax) + np.abs(ref)) * 1.01
+    err = np.abs(y - ref)
+    assert np.all(err <= bound), (name, int(np.argmax(err / np.maximum(bound, 1e-300))), float(np.max(err / bound)))
+    # the bound is not vacuous: the worst element uses a good part of it
+    assert np.max(err / bound) > 0.02
 
 
 def test_fp32_vectors_with_double_float_sums(env):
