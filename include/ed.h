@@ -225,8 +225,8 @@ int ed_dot(ed_ctx* ctx, const void* x, const void* y, uint64_t n, int prec, doub
  * 268,435,456 elements (65,536 tiles of 4,096) and a larger n is rejected with
  * ED_ERR_INVALID before any device work.  It calls no cudaMalloc or cudaFree.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  With CUDA's lazy module loading (the default since CUDA
+ * (cudaGetSymbolAddress) with that device current.  With CUDA's lazy module
+ * loading (the default since CUDA
  * 12.2) that first look-up is also what loads the library module holding the
  * array onto the device, so the array's 512 KB become resident at the first
  * call, not when the library is loaded: a caller that will later hand all free
